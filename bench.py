@@ -1,0 +1,416 @@
+#!/usr/bin/env python
+"""Benchmark of the GPU ADMM QP solver on a synthetic workload shaped like
+the paper's Lasso class (D: 100000 x 1000 at 15% density, ~15.1M nonzeros in
+A), solved to eps_abs = eps_rel = 1e-3 with FP32 PCG and FP64 reductions.
+
+One step = osqp_setup from device-resident CSR inputs (validation, A' and
+[P A'] construction, Ruiz equilibration, preconditioner) + osqp_solve (the
+whole ADMM loop as one CUDA graph) + the unscaled solution written to device
+buffers.  value = solves per second over all ranks (replicas, one problem
+per GPU, seed + rank).
+
+Also reported: the same metric end to end from pinned host buffers through
+the C ABI (e2e), the plain FP64 form, ADMM iterations/s, the roofline of the
+dominant kernel (CUDA events, algorithmic bytes), SM clocks sampled during
+the timed region, and the FP64 CPU oracle timed on the host (cpu_baseline).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-3 solve & ADMM it/s (learned FP32 vs plain FP64); SpMV GB/s"
+WORKLOAD = "lasso_1000x100000"
+WORKLOAD_TEXT = ("Lasso QP (configs[1] shape): D 100000x1000 at 15% density N(0,1), "
+                 "variables (x, y, t), n = m = 102000, eps_abs = eps_rel = 1e-3")
+HBM_FALLBACK_GBS = 6800.0
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+# ------------------------------------------------------------- CPU leg --
+
+def cpu_leg(workload: str, seed: int) -> dict:
+    """The FP64 oracle (direct LDL' ADMM, as it stands) on one instance."""
+    import qpgen
+    from oracle import admm
+    qp = qpgen.by_name(workload, seed)
+    t = time.perf_counter()
+    r = admm.solve(qp)
+    dt = time.perf_counter() - t
+    return {"seconds": dt, "status": r.status, "iters": r.iters, "obj": r.obj}
+
+
+def run_cpu_leg(workload: str, seed: int) -> dict:
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = "1"
+    p = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-leg", "--workload", workload,
+                        "--seed", str(seed)], capture_output=True, text=True, env=env, cwd=ROOT)
+    if p.returncode != 0:
+        raise RuntimeError("cpu leg failed:\n" + p.stderr[-2000:])
+    return json.loads(p.stdout.strip().splitlines()[-1])
+
+
+# --------------------------------------------------------------- clocks --
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- GPU arm --
+
+def algorithmic_bytes(kernel: str, n: int, m: int, nnz: int, s: int = 4) -> int:
+    """Bytes one launch must move at minimum: matrix values and column
+    indices once, row pointers once, the gathered vector once, the row
+    outputs once, and the extra vectors the kernel's epilogue reads."""
+    if kernel == "pcg_kapply":  # rows n of [P A']; gathers [p; t]; writes Kp; reads p
+        return nnz * (s + 4) + (n + 1) * 4 + (n + m) * s + n * s + n * s
+    if kernel == "pcg_direction":  # rows m of A; gathers yv, pc (n each); writes t (m) and p (n)
+        return nnz * (s + 4) + (m + 1) * 4 + 2 * n * s + m * s + n * s
+    raise ValueError(kernel)
+
+
+def gpu_arm(args) -> None:
+    import numpy as np
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0:
+        import __graft_entry__
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    import qpgen
+    from paper_1912_04263_gb300 import binding as gb
+
+    qp = qpgen.by_name(args.workload, args.seed + rank)
+    n, m = qp.n, qp.m
+    dev = torch.device("cuda", local)
+    P, A = qp.P.tocsr(), qp.A.tocsr()
+    import numpy as _np
+    lo = _np.where(_np.isinf(qp.l), _np.sign(qp.l) * 1e20, qp.l)
+    hi = _np.where(_np.isinf(qp.u), _np.sign(qp.u) * 1e20, qp.u)
+    host = {"Prp": _np.ascontiguousarray(P.indptr, _np.int64), "Pcol": _np.ascontiguousarray(P.indices, _np.int32),
+            "Pval": _np.ascontiguousarray(P.data, _np.float64), "Arp": _np.ascontiguousarray(A.indptr, _np.int64),
+            "Acol": _np.ascontiguousarray(A.indices, _np.int32), "Aval": _np.ascontiguousarray(A.data, _np.float64),
+            "q": _np.ascontiguousarray(qp.q), "l": _np.ascontiguousarray(lo), "u": _np.ascontiguousarray(hi)}
+    devt = {k: torch.from_numpy(v).to(dev) for k, v in host.items()}
+    pinned = {k: torch.from_numpy(v).pin_memory() for k, v in host.items()}
+    h2d_bytes = sum(v.numel() * v.element_size() for v in pinned.values())
+    d2h_bytes = (n + 2 * m) * 8
+    xo = torch.empty(n, dtype=torch.float64, device=dev)
+    yo = torch.empty(m, dtype=torch.float64, device=dev)
+    zo = torch.empty(m, dtype=torch.float64, device=dev)
+    # a dedicated stream: the library runs on it and the CUDA events are
+    # recorded on it (torch's default stream would be handle 0, which the
+    # library treats as "create your own")
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.synchronize()
+
+    def settings(prec):
+        s = gb.default_settings(precision=prec, device=local)
+        s.cuda_stream = stream.cuda_stream
+        if args.loop == "host":
+            s.loop_mode = gb.LOOP_HOST
+        return s
+
+    def setup_device(prec):
+        return gb.osqp_setup_device(devt["Prp"], devt["Pcol"], devt["Pval"], devt["Arp"], devt["Acol"],
+                                    devt["Aval"], devt["q"], devt["l"], devt["u"], n, m, settings(prec))
+
+    def step(prec):
+        h = setup_device(prec)
+        st = gb.osqp_solve(h)
+        gb.gbosqp_get_solution_device(h, xo, yo, zo)
+        return h, st
+
+    def setup_host(prec):
+        s = settings(prec)
+        s.P_is_upper = 0
+        s.input_location = gb.HOST
+        cp = gb.Csr(n, n, int(P.nnz), pinned["Prp"].data_ptr(), pinned["Pcol"].data_ptr(), pinned["Pval"].data_ptr())
+        ca = gb.Csr(m, n, int(A.nnz), pinned["Arp"].data_ptr(), pinned["Acol"].data_ptr(), pinned["Aval"].data_ptr())
+        h = gb.ctypes.c_void_p()
+        rc = gb.lib().osqp_setup(gb.ctypes.byref(h), gb.ctypes.byref(cp), gb.ctypes.byref(ca),
+                                 pinned["q"].data_ptr(), pinned["l"].data_ptr(), pinned["u"].data_ptr(),
+                                 gb.ctypes.byref(s))
+        if rc != gb.OK:
+            raise gb.GbosqpError(rc, gb.lib().gbosqp_setup_error().decode())
+        return h.value
+
+    xh = np.empty(n)
+    yh = np.empty(m)
+    zh = np.empty(m)
+
+    def step_e2e(prec):
+        h = setup_host(prec)
+        st = gb.osqp_solve(h)
+        gb.lib().osqp_get_solution(h, xh.ctypes.data, yh.ctypes.data, zh.ctypes.data)
+        return h, st
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    def timed(fn, prec, steps):
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        hs = []
+        e0.record(stream)
+        for _ in range(steps):
+            hs.append(fn(prec))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        infos = [gb.osqp_get_info(h) for h, _ in hs]
+        stats = [st for _, st in hs]
+        return ms, infos, stats, [h for h, _ in hs]
+
+    def maxrank(v):
+        if not dist:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # warm-up
+    for _ in range(args.warmup):
+        h, _ = step(gb.FP32)
+        gb.osqp_cleanup(h)
+    if args.lean:  # one untimed-by-events step, for profiler launch lists
+        h, st = step(gb.FP32)
+        torch.cuda.synchronize()
+        info = gb.osqp_get_info(h)
+        gb.osqp_cleanup(h)
+        if rank == 0:
+            print(json.dumps({"lean": True, "status": st, "iters": info["iters"], "pcg_iters": info["pcg_iters"],
+                              "setup_launches": info["setup_launches"], "solve_launches": info["solve_launches"]}))
+        return
+    clock = ClockSampler(local)
+    clock.start()
+    ms, infos, stats, handles = timed(step, gb.FP32, args.steps)
+    clocks = clock.stop()
+    ms_step = maxrank(ms) / args.steps
+    keep = handles[0]
+    for h in handles[1:]:
+        gb.osqp_cleanup(h)
+
+    # roofline of the dominant kernels on a live handle (CUDA events)
+    reps = 50
+    n_, m_, nnz_a, nnz_pat = gb.dims(keep)
+    k_ms = {"pcg_kapply": gb.gbosqp_bench_kernel(keep, gb.K_PCG_KAPPLY, reps),
+            "pcg_direction": gb.gbosqp_bench_kernel(keep, gb.K_PCG_DIRECTION, reps),
+            "pcg_update": gb.gbosqp_bench_kernel(keep, gb.K_PCG_UPDATE, reps)}
+    gbs = {"pcg_kapply": algorithmic_bytes("pcg_kapply", n_, m_, nnz_pat) / (k_ms["pcg_kapply"] * 1e-3) / 1e9,
+           "pcg_direction": algorithmic_bytes("pcg_direction", n_, m_, nnz_a) / (k_ms["pcg_direction"] * 1e-3) / 1e9}
+    dominant = max(("pcg_kapply", "pcg_direction"), key=lambda k: k_ms[k])
+    gb.osqp_cleanup(keep)
+
+    # end to end from pinned host memory
+    for _ in range(max(1, args.warmup // 2)):
+        h, _ = step_e2e(gb.FP32)
+        gb.osqp_cleanup(h)
+    e2e_ms, _, e2e_stats, hs = timed(step_e2e, gb.FP32, max(1, args.steps // 2))
+    for h in hs:
+        gb.osqp_cleanup(h)
+    e2e_step = maxrank(e2e_ms) / max(1, args.steps // 2)
+
+    # plain FP64 form
+    fp64_ms, fp64_infos, fp64_stats, hs = timed(step, gb.FP64, max(1, args.steps // 2))
+    for h in hs:
+        gb.osqp_cleanup(h)
+    fp64_step = maxrank(fp64_ms) / max(1, args.steps // 2)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    hbm, peak_kind = peaks()
+    med = lambda key, arr: statistics.median([i[key] for i in arr])  # noqa: E731
+    iters = med("iters", infos)
+    solve_ms = med("solve_ms", infos)
+    launches = int(sum(i["setup_launches"] + i["solve_launches"] for i in infos))
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.txt")
+    if os.path.exists(tpath):
+        for line in open(tpath):
+            parts = line.split()
+            if len(parts) >= 3 and parts[0] == dominant and parts[1] == args.workload:
+                traffic = float(parts[2])
+    out = {
+        "metric": METRIC,
+        "value": world * 1000.0 / ms_step,
+        "unit": "solves/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 (f64 reductions)",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT, "name": args.workload, "seed": args.seed, "n": n, "m": m,
+                   "nnz_A": int(A.nnz), "nnz_P": int(P.nnz), "precision": "fp32", "rho_policy": "ratio",
+                   "step": "osqp_setup(device CSR) + osqp_solve + solution to device",
+                   "l2": "no flush: each step streams >240 MB of matrices, above the 129 MB L2",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "status": sorted(set(int(s) for s in stats)),
+        "time_to_1e3_s": ms_step / 1000.0,
+        "solve_ms": solve_ms,
+        "setup_ms": med("setup_ms", infos),
+        "admm_iters": iters,
+        "pcg_iters": med("pcg_iters", infos),
+        "admm_it_per_s": iters / (solve_ms / 1000.0),
+        "spmv_gbs": {k: round(v, 1) for k, v in gbs.items()},
+        "kernel_ms": {k: round(v, 5) for k, v in k_ms.items()},
+        "plain_fp64": {"time_to_1e3_s": fp64_step / 1000.0, "status": sorted(set(int(s) for s in fp64_stats)),
+                       "admm_iters": med("iters", fp64_infos), "pcg_iters": med("pcg_iters", fp64_infos),
+                       "solve_ms": med("solve_ms", fp64_infos)},
+        "roofline": {"bound": "hbm", "kernel": dominant, "achieved": round(gbs[dominant], 1), "peak": hbm,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": round(gbs[dominant] / hbm, 4),
+                     "traffic": traffic,
+                     "algorithmic_bytes": algorithmic_bytes(dominant, n_, m_, nnz_pat if dominant == "pcg_kapply" else nnz_a)},
+        "e2e": {"value": world * 1000.0 / e2e_step, "unit": "solves/s", "ms_per_step": e2e_step,
+                "h2d_bytes_per_step": int(h2d_bytes), "d2h_bytes_per_step": int(d2h_bytes)},
+        "clocks": clocks,
+        "gpu_launches": launches,
+    }
+    if not args.no_cpu_baseline:
+        try:
+            c = run_cpu_leg(args.workload, args.seed)
+            out["cpu_baseline"] = {"value": 1.0 / c["seconds"], "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                   "sample": f"one full FP64 direct-LDL' ADMM solve to 1e-3 of the same instance "
+                                             f"(Ruiz, factorization, {c['iters']} iterations), single thread",
+                                   "seconds": c["seconds"], "status": c["status"]}
+        except Exception as e:  # keep the GPU line
+            out["cpu_baseline"] = {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                   "sample": "failed: " + str(e)[:200]}
+    print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+def reference_arm(args) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    c = run_cpu_leg(args.workload, args.seed)
+    v = 1.0 / c["seconds"]
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s",
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": 1, "warmup": 0,
+        "ms_per_step": c["seconds"] * 1000.0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_TEXT, "name": args.workload, "seed": args.seed,
+                   "step": "one full FP64 oracle solve (direct LDL' ADMM); one timed step regardless of --steps "
+                           "because one solve takes about a minute on one core"},
+        "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": "one full solve of the same instance, single thread"},
+        "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "status": c["status"], "iters": c["iters"],
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-leg", action="store_true")
+    ap.add_argument("--lean", action="store_true", help="warm-up steps then one step, minimal output (profiling)")
+    ap.add_argument("--loop", default="graph", choices=["graph", "host"],
+                    help="host: the same kernels driven by a host loop (profilers cannot attribute kernel "
+                         "nodes inside graphs with conditional nodes)")
+    args = ap.parse_args()
+    if args.cpu_leg:
+        print(json.dumps(cpu_leg(args.workload, args.seed)))
+        return
+    if args.warmup < 3 and args.impl == "ours" and not args.lean:
+        args.warmup = 3
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

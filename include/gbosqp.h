@@ -1,0 +1,281 @@
+/*
+ * gbosqp: ADMM solver for sparse convex QPs on one NVIDIA GB300 (sm_103a).
+ *
+ *     minimize    1/2 x'Px + q'x
+ *     subject to  l <= Ax <= u                      (paper Section 2, eq. (qp))
+ *
+ * The method is Algorithm 1 (OSQP) of Schubiger, Banjac & Lygeros, "GPU
+ * Acceleration of ADMM for Large-Scale Quadratic Programming", with the
+ * linear-system step solved on the reduced KKT system eq. (kkt_red_sc),
+ * (P + sigma I + rho A'A) x~ = sigma x - q + A'(rho z - y), by warm-started
+ * Jacobi-preconditioned conjugate gradient (Algorithm 3, Section 5.3), after
+ * Ruiz equilibration (Algorithm 2, Section 5.4), with R = rho I, termination
+ * checked every 5 iterations and rho adapted every 10 (Table 1).
+ *
+ * Conventions shared by every call:
+ *   - Matrices are CSR with 64-bit row pointers and 32-bit column indices,
+ *     zero-based, columns strictly increasing within each row (no
+ *     duplicates), values double.  Internally nnz must be < 2^31 per matrix.
+ *   - Bounds with |v| >= GBOSQP_INFINITY (or +-inf) are infinite.  l <= u.
+ *   - Unless a call says otherwise, vector arguments are host pointers to
+ *     double, caller-owned, of the stated length; the library copies what it
+ *     needs and never keeps a caller pointer past the call.
+ *   - Calls return GBOSQP_OK (0) or a negative GBOSQP_ERR_* code; they never
+ *     abort the process.  gbosqp_last_error() describes the last failure of a
+ *     handle.  A handle is not thread safe: one caller thread at a time.
+ *   - All device work runs on the stream given in the settings (or on a
+ *     stream the library creates); calls that return host data synchronise
+ *     that stream.
+ */
+#ifndef GBOSQP_H
+#define GBOSQP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes (negative) ------------------------------------------ */
+#define GBOSQP_OK 0
+#define GBOSQP_ERR_INVALID_ARG (-1)   /* NULL pointer, bad setting value      */
+#define GBOSQP_ERR_DIMENSION (-2)     /* shapes of P, A, q, l, u disagree     */
+#define GBOSQP_ERR_CSR (-3)           /* bad row pointers, unsorted or
+                                         duplicate or out-of-range columns,
+                                         lower entries in an upper P          */
+#define GBOSQP_ERR_BOUNDS (-4)        /* l_i > u_i or NaN bound               */
+#define GBOSQP_ERR_NONFINITE (-5)     /* NaN or inf in P, A or q              */
+#define GBOSQP_ERR_CUDA (-6)          /* a CUDA runtime call failed           */
+#define GBOSQP_ERR_OOM (-7)           /* device allocation failed             */
+#define GBOSQP_ERR_DEVICE_TIMEOUT (-8)/* a bounded device wait gave up        */
+#define GBOSQP_ERR_UNSUPPORTED (-9)   /* e.g. nnz >= 2^31, no sm_103a device  */
+#define GBOSQP_ERR_POLICY (-10)       /* learned policy parameters invalid    */
+
+/* ---- solve status (positive) ------------------------------------------ */
+#define GBOSQP_SOLVED 1               /* residuals within eq. (termination)  */
+#define GBOSQP_MAX_ITER 2             /* max_iter reached                     */
+#define GBOSQP_NONFINITE 3            /* NaN/inf appeared in the iterates     */
+#define GBOSQP_PRIMAL_INFEASIBLE 4    /* reserved: certificate eq. (prim_infeas) */
+#define GBOSQP_DUAL_INFEASIBLE 5      /* reserved: certificate eq. (dual_infeas) */
+
+/* ---- enumerations ------------------------------------------------------ */
+#define GBOSQP_FP32 0                 /* matrices and vectors in FP32, PCG dot
+                                         products and residual reductions in FP64 */
+#define GBOSQP_FP64 1                 /* everything in FP64                   */
+
+#define GBOSQP_RHO_RATIO 0            /* residual-ratio rule, Section 3.4     */
+#define GBOSQP_RHO_LEARNED 1          /* MLP policy with ratio-rule fallback  */
+#define GBOSQP_RHO_FIXED 2            /* rho never changes                    */
+
+#define GBOSQP_HOST 0                 /* input arrays are host memory         */
+#define GBOSQP_DEVICE 1               /* input arrays are device memory of the
+                                         settings' device                     */
+
+#define GBOSQP_LOOP_GRAPH 0           /* whole solve = one CUDA graph launch
+                                         (conditional while nodes; no host
+                                         synchronisation inside the solve)   */
+#define GBOSQP_LOOP_HOST 1            /* same kernels driven by a host loop
+                                         that reads the stop flags (debug)    */
+
+#define GBOSQP_INFINITY 1e20
+
+/* Matrix selectors for the inspection calls. */
+#define GBOSQP_MAT_A 0                /* scaled A, m x n                      */
+#define GBOSQP_MAT_PAT 1              /* scaled [P  A'], n x (n + m): row i
+                                         holds row i of the full P followed by
+                                         row i of A' (columns offset by n)    */
+
+/* Number of doubles written by gbosqp_check(). */
+#define GBOSQP_CHECK_FIELDS 16
+
+/* ---- structures -------------------------------------------------------- */
+typedef struct {
+    int32_t nrows, ncols;
+    int64_t nnz;
+    const int64_t *rowptr; /* nrows + 1 */
+    const int32_t *colind; /* nnz */
+    const double *val;     /* nnz */
+} gbosqp_csr;
+
+typedef struct {
+    double alpha;        /* relaxation, in ]0, 2[            default 1.6  */
+    double sigma;        /* > 0                              default 1e-6 */
+    double rho0;         /* initial rho, > 0                 default 0.1  */
+    double eps_abs;      /* >= 0                             default 1e-3 */
+    double eps_rel;      /* >= 0                             default 1e-3 */
+    double pcg_lambda;   /* in ]0, 1[, Section 5.3.4         default 0.15 */
+    double pcg_eps_min;  /* > 0                              default 1e-7 */
+    double rho_min;      /* clamp of adapted rho             default 1e-6 */
+    double rho_max;      /*                                  default 1e6  */
+    int32_t max_iter;    /* ADMM iterations (rounded up to a multiple of
+                            check_every)                     default 4000 */
+    int32_t max_cg_iter; /* PCG steps per ADMM iteration     default 50   */
+    int32_t check_every; /* termination check period, 1..16  default 5    */
+    int32_t rho_every;   /* rho period, multiple of check_every, default 10 */
+    int32_t scaling_iters; /* Ruiz passes, 0..100            default 10   */
+    int32_t precision;   /* GBOSQP_FP32 | GBOSQP_FP64        default FP32 */
+    int32_t rho_policy;  /* GBOSQP_RHO_*                     default RATIO */
+    int32_t P_is_upper;  /* 1: P holds only its upper triangle (OSQP
+                            convention); 0: P is the full symmetric matrix
+                                                             default 1    */
+    int32_t input_location; /* GBOSQP_HOST | GBOSQP_DEVICE   default HOST */
+    int32_t loop_mode;   /* GBOSQP_LOOP_*                    default GRAPH */
+    int32_t device;      /* CUDA device ordinal              default 0    */
+    int32_t reserved0;
+    void *cuda_stream;   /* cudaStream_t to run on; NULL: the library
+                            creates and owns one             default NULL */
+    const float *policy_params; /* learned policy parameters (host, FP32,
+                                   GBOSQP_POLICY_PARAMS floats) or NULL    */
+} gbosqp_settings;
+
+/* Layout of the learned-policy parameter vector (see gbosqp_policy.h). */
+#define GBOSQP_POLICY_PARAMS 4622
+
+typedef struct {
+    int32_t status;      /* GBOSQP_SOLVED ... or 0 before the first solve  */
+    int32_t iters;       /* ADMM iterations                                */
+    int64_t pcg_iters;   /* PCG steps summed over the solve                */
+    double obj;          /* 1/2 x'Px + q'x at the returned x               */
+    double r_prim;       /* ||Ax - z||_inf (unscaled, last check)          */
+    double r_dual;       /* ||Px + q + A'y||_inf (unscaled, last check)    */
+    double eps_prim;     /* tolerances of the last check                    */
+    double eps_dual;
+    double rho;          /* rho at the end of the solve                    */
+    double pcg_eps;      /* PCG tolerance at the end of the solve          */
+    double setup_ms;     /* wall time of osqp_setup                         */
+    double solve_ms;     /* device time of the last osqp_solve             */
+    int32_t rho_updates; /* number of rho changes                          */
+    int32_t policy_fallbacks; /* learned policy: checks that used the ratio rule */
+    int64_t nnz_P;       /* full P                                          */
+    int64_t nnz_A;
+    int64_t setup_launches; /* kernels launched by osqp_setup              */
+    int64_t solve_launches; /* kernels executed by the last osqp_solve
+                               (graph nodes included)                      */
+} gbosqp_info;
+
+typedef struct gbosqp_handle gbosqp_handle;
+
+/* ---- core calls (paper: Algorithm 1 with Section 5 on the GPU) --------- */
+
+/* Fill *s with the defaults above.  Returns GBOSQP_OK. */
+int gbosqp_default_settings(gbosqp_settings *s);
+
+/* Validate the problem, copy it to the device, build P (full), A' (stored
+ * explicitly, Section 5.2) and the concatenated [P A'] in CSR, run Ruiz
+ * equilibration (Algorithm 2) on the device, compute the Jacobi
+ * preconditioner data (Section 5.3.1), and build the solve graph.
+ * P: n x n (upper triangle or full, see P_is_upper), A: m x n, q: n, l, u: m.
+ * Memory location of all inputs: settings->input_location.  On success *out
+ * owns all device memory until osqp_cleanup.  On failure *out is NULL and
+ * the code says why (no handle exists to query gbosqp_last_error; the text
+ * is available from gbosqp_setup_error()). */
+int osqp_setup(gbosqp_handle **out, const gbosqp_csr *P, const gbosqp_csr *A, const double *q,
+               const double *l, const double *u, const gbosqp_settings *settings);
+
+/* Run ADMM from a cold start (x = z = y = 0, rho = rho0) or from the point
+ * given by osqp_warm_start, until eq. (termination) holds, max_iter, or
+ * non-finite iterates.  Returns the status (> 0) or an error (< 0).  The
+ * unscaled solution stays on the device until fetched. */
+int osqp_solve(gbosqp_handle *h);
+
+/* Set rho (Section 5.3.3): only the Jacobi preconditioner is recomputed;
+ * no factorization exists.  The next osqp_solve starts from this rho.
+ * rho must be > 0 and finite. */
+int osqp_update_rho(gbosqp_handle *h, double rho);
+
+/* Make the next osqp_solve start from x (n) and y (m) (unscaled, host);
+ * z starts at the projection of Ax onto [l, u].  Either may be NULL (zero). */
+int osqp_warm_start(gbosqp_handle *h, const double *x, const double *y);
+
+/* Copy the unscaled solution of the last solve to host arrays x (n), y (m),
+ * z (m); any may be NULL. */
+int osqp_get_solution(const gbosqp_handle *h, double *x, double *y, double *z);
+
+/* The same, into device arrays of the handle's device (no host copy). */
+int gbosqp_get_solution_device(const gbosqp_handle *h, double *x, double *y, double *z);
+
+/* Solver statistics of the last solve. */
+int osqp_get_info(const gbosqp_handle *h, gbosqp_info *info);
+
+/* Free everything the handle owns.  NULL is accepted. */
+void osqp_cleanup(gbosqp_handle *h);
+
+/* Text of the last error on h (never NULL). */
+const char *gbosqp_last_error(const gbosqp_handle *h);
+
+/* Text of the last osqp_setup failure in this thread (never NULL). */
+const char *gbosqp_setup_error(void);
+
+/* Static text for a return code or status. */
+const char *gbosqp_error_string(int code);
+
+/* Problem sizes of a handle (any pointer may be NULL). */
+int gbosqp_dims(const gbosqp_handle *h, int32_t *n, int32_t *m, int64_t *nnz_A, int64_t *nnz_PAt);
+
+/* ---- inspection and step-level calls (used by the parity tests) ------- *
+ * These expose single steps of the method on the handle's scaled problem so
+ * that each can be compared with an independent implementation.  They
+ * change the handle's iterates only where stated. */
+
+/* Ruiz scaling of Algorithm 2: D (n), E (m), c. */
+int gbosqp_get_scaling(const gbosqp_handle *h, double *D, double *E, double *c);
+
+/* Download a scaled matrix (GBOSQP_MAT_A or GBOSQP_MAT_PAT) in CSR with
+ * values in double (rounded from FP32 on the FP32 path).  Sizes from
+ * gbosqp_dims: rowptr nrows+1, colind and val nnz. */
+int gbosqp_get_scaled_csr(const gbosqp_handle *h, int which, int64_t *rowptr, int32_t *colind,
+                          double *val);
+
+/* y = M x with the device SpMV kernel (Section 4.3.2 CSR; load-balanced row
+ * blocks) for M = GBOSQP_MAT_A (x: n, y: m) or GBOSQP_MAT_PAT (x: n + m,
+ * y: n).  x is rounded to the working precision; fp64_accumulate selects
+ * FP64 row accumulation (as in the termination check) instead of the working
+ * precision (as in PCG). */
+int gbosqp_spmv(gbosqp_handle *h, int which, const double *x, double *y, int fp64_accumulate);
+
+/* Algorithm 3 on the device for K = P + sigma I + rho A'A (scaled data) with
+ * the Jacobi preconditioner for rho: start from x0 (n), stop when
+ * ||K x - b||_inf <= eps or after max_iter steps.  Writes x (n), the step
+ * count and the final ||r||_inf.  Does not touch the ADMM iterates. */
+int gbosqp_pcg(gbosqp_handle *h, double rho, const double *b, const double *x0, double eps,
+               int32_t max_iter, double *x, int32_t *iters, double *r_norm);
+
+/* Set / get the scaled ADMM state: x (n), z (m), y (m), the PCG warm start
+ * x~ (n) and rho.  set also recomputes z~ = A x~ and the preconditioner. */
+int gbosqp_set_iterates(gbosqp_handle *h, const double *x, const double *z, const double *y,
+                        const double *xt, double rho);
+int gbosqp_get_iterates(const gbosqp_handle *h, double *x, double *z, double *y, double *xt,
+                        double *rho);
+
+/* Run k ADMM iterations from the current state with the host-driven loop
+ * (same kernels as the graph), checks and rho updates included, without the
+ * cold-start reset.  Writes the number of PCG steps of each iteration to
+ * pcg_per_iter (k entries, may be NULL).  Returns status or error. */
+int gbosqp_admm_iterations(gbosqp_handle *h, int32_t k, int32_t *pcg_per_iter);
+
+/* Evaluate the termination check at the current state and write, in order:
+ * r_prim, r_dual, eps_prim, eps_dual (unscaled, Section 3.1), the scaled
+ * r_prim, r_dual, ||Ax||, ||z||, ||Px||, ||A'y||, ||q|| (used by the rho
+ * rule and the PCG tolerance), the objective, and 4 reserved zeros. */
+int gbosqp_check(gbosqp_handle *h, double out[GBOSQP_CHECK_FIELDS]);
+
+/* Kernel selectors for gbosqp_bench_kernel. */
+#define GBOSQP_K_PCG_DIRECTION 0  /* p = -M^{-1}r + beta p, t = rho A p (SpMV A)        */
+#define GBOSQP_K_PCG_KAPPLY 1     /* K p = P p + sigma p + A' t, p'Kp (SpMV [P A'])     */
+#define GBOSQP_K_PCG_UPDATE 2     /* x, r, M^{-1} r updates, r'y, ||r|| (vectors, n)    */
+#define GBOSQP_K_PCG_INIT 3       /* r = K x - b from [P A'] and t0 (SpMV [P A'])       */
+#define GBOSQP_K_ADMM_UPDATE 4    /* z~ = A x~, projection, dual update (SpMV A)        */
+#define GBOSQP_K_CHECK_A 5        /* ||Ax - z|| etc., FP64 accumulation (SpMV A)        */
+#define GBOSQP_K_CHECK_B 6        /* ||Px + q + A'y|| etc., FP64 (SpMV [P A'])          */
+
+/* Time `reps` back-to-back launches of one solve kernel on the handle's
+ * stream with CUDA events, in the launch configuration the solve uses, on
+ * the handle's current vectors (a private copy of the scalar state is used,
+ * so the next solve is unaffected).  Writes the mean duration in ms. */
+int gbosqp_bench_kernel(gbosqp_handle *h, int kernel, int32_t reps, double *avg_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBOSQP_H */

@@ -22,7 +22,8 @@ class KKTViolation:
     prim: float          # ||Ax - z||_inf                      (prim_feas)
     dual: float          # ||Px + q + A'y||_inf                (dual_feas)
     box: float           # max violation of l <= z <= u        (box_constr)
-    compl: float         # max |min(y,0)(z-l)|, |max(y,0)(z-u)| (compl_slack)
+    compl: float         # max |min(y,0)(z-l)|, |max(y,0)(z-u)| (compl_slack);
+                         # |min(y,0)| where l = -inf, |max(y,0)| where u = +inf
 
 
 def kkt_violation(qp, x, z, y) -> KKTViolation:
@@ -32,11 +33,22 @@ def kkt_violation(qp, x, z, y) -> KKTViolation:
     box = float(max(np.max(l - z, initial=0.0), np.max(z - u, initial=0.0), 0.0))
     yneg = np.minimum(y, 0.0)
     ypos = np.maximum(y, 0.0)
+    # with an infinite bound eq. (compl_slack) can only hold with a zero
+    # multiplier on that side, so the violation there is the multiplier
     with np.errstate(invalid="ignore"):
-        cl = np.where(np.isinf(l), np.where(yneg != 0.0, np.inf, 0.0), yneg * (z - l))
-        cu = np.where(np.isinf(u), np.where(ypos != 0.0, np.inf, 0.0), ypos * (z - u))
+        cl = np.where(np.isinf(l), yneg, yneg * (z - l))
+        cu = np.where(np.isinf(u), ypos, ypos * (z - u))
     compl = float(max(np.max(np.abs(cl), initial=0.0), np.max(np.abs(cu), initial=0.0)))
     return KKTViolation(prim, dual, box, compl)
+
+
+def objective_error_bound(x, y, r_prim, r_dual, x_star, y_star) -> float:
+    """Bound on |f(x) - f*| for an iterate whose (z, y) satisfy the box and
+    complementarity conditions exactly (as ADMM's projection step ensures),
+    from convexity: f(x) - f* >= -||y*||_1 ||Ax - z||_inf and
+    f(x) - f* <= ||Px + q + A'y||_inf ||x - x*||_1 + ||y||_1 ||Ax - z||_inf."""
+    return float(max(np.sum(np.abs(y_star)), np.sum(np.abs(y))) * r_prim
+                 + r_dual * np.sum(np.abs(np.asarray(x) - np.asarray(x_star))))
 
 
 def duality_gap(qp, x, y) -> float:

@@ -1,0 +1,398 @@
+// Shared device and host machinery of the gbosqp library.
+//
+// * Error handling: host code throws GbError; every extern "C" entry point
+//   catches it and returns the code.
+// * DevBuf: owning device allocation.
+// * Status: the device-resident scalar block of a solve (rho, PCG scalars,
+//   check results, flags), so that the iteration loop needs no host
+//   round trip (north of Algorithm 1: every decision is taken on the device).
+// * Row-block CSR SpMV: the rows of a CSR matrix are cut at set-up into work
+//   items of at most kCap nonzeros (consecutive short rows), and rows longer
+//   than kCap are cut into pieces whose partial sums are combined in a fixed
+//   order by the last piece to finish.  A CTA streams an item's contiguous
+//   value/column range with coalesced loads, multiplies by the gathered
+//   vector into shared memory, then reduces each row with a lane group sized
+//   to the item's mean row length.  Results are bitwise reproducible.
+// * Block reductions with a last-block finalize: per-CTA partials are summed
+//   in CTA order by the last CTA to finish (FP64 sums, NaN-propagating max).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <tuple>
+#include <utility>
+#include <vector>
+
+#include "../../include/gbosqp.h"
+
+namespace gb {
+
+// ------------------------------------------------------------------ errors
+
+struct GbError {
+    int code;
+    std::string msg;
+};
+
+[[noreturn]] void fail(int code, const std::string &msg);
+void check_cuda(cudaError_t e, const char *what, const char *file, int line);
+#define GB_CUDA(call) ::gb::check_cuda((call), #call, __FILE__, __LINE__)
+
+// ----------------------------------------------------------------- buffers
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    explicit DevBuf(size_t nbytes) { alloc(nbytes); }
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    DevBuf(DevBuf &&o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+    DevBuf &operator=(DevBuf &&o) noexcept {
+        if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+        return *this;
+    }
+    ~DevBuf() { release(); }
+    void alloc(size_t nbytes);
+    void release();
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// -------------------------------------------------------------- constants
+
+constexpr int kThreads = 256;             // CTA size of every row-block kernel
+constexpr int kWarps = kThreads / 32;
+constexpr int kCap = 2048;                // max nonzeros per work item
+constexpr int kPerThread = kCap / kThreads;
+constexpr double kInf = 1e20;             // |bound| >= kInf is infinite
+
+// ------------------------------------------------------------ SpMV items
+
+struct Item {
+    int r0;  // first row (block) or the long row (piece)
+    int r1;  // one past the last row (block, >= 0) or -(long-row id + 1)
+    int k0;  // first nonzero
+    int k1;  // one past the last nonzero
+};
+
+struct LongRow {
+    int first_item;
+    int npieces;
+};
+
+// Host-side plan of one matrix: items and the long-row table.
+struct HostPlan {
+    std::vector<Item> items;
+    std::vector<LongRow> longrows;
+};
+HostPlan build_plan(const std::vector<int> &rowptr);
+
+// Device view of a CSR matrix with its plan.  pend (optional) splits each
+// row into two segments [rowptr[r], pend[r]) and [pend[r], rowptr[r+1]).
+template <class T>
+struct CsrDev {
+    int nrows = 0, ncols = 0;
+    const int *rowptr = nullptr;
+    const int *col = nullptr;
+    const T *val = nullptr;
+    const int *pend = nullptr;
+    const Item *items = nullptr;
+    int nitems = 0;
+    const LongRow *longrows = nullptr;
+    int *lr_count = nullptr;     // one ticket counter per long row (zeroed)
+    double *lr_part = nullptr;   // 2 partial sums per item
+};
+
+// ------------------------------------------------------------ status block
+
+enum StatusSlot { kC1RpS = 0, kC1AxS, kC1ZS, kC1RpU, kC1AxU, kC1ZU, kC1N };
+
+struct Status {
+    // problem constants
+    double sigma, alpha, eps_abs, eps_rel, lambda, eps_min, rho_min, rho_max;
+    double rho0, c, cinv, eps0, qnorm_s, qnorm_u;
+    int n, m, max_iter, max_cg, check_every, rho_every, policy, warm;
+    // evolving
+    double rho, eps_pcg;
+    double ry, pkp, alpha_cg, beta, rnorm;
+    int cg_it, breakdown, pcg_continue, admm_continue;
+    long long cg_total;
+    int k, rho_changed, rho_updates, status;
+    // termination check
+    double c1[kC1N];
+    double r_prim, r_dual, eps_prim, eps_dual;
+    double rp_s, rd_s, ax_s, z_s, px_s, aty_s, obj;
+    // learned policy
+    int fallbacks, stall_count, stall_left, policy_disabled;
+    double last_merit, prev_merit;
+    int cg_since_update, pad0;
+    // last-block tickets, one per kernel kind
+    unsigned int tickets[16];
+};
+
+enum Ticket { kTkI1 = 0, kTkK2, kTkK3, kTkC1, kTkC2, kTkSetupA, kTkSetupB, kTkSetupC, kTkMisc };
+
+// ------------------------------------------------------------- reductions
+
+__device__ __forceinline__ double nanmax(double a, double b) {
+    return (a != a) ? a : ((b != b) ? b : (a > b ? a : b));
+}
+
+template <int NS, int NM>
+struct Red {
+    double s[NS > 0 ? NS : 1];
+    double m[NM > 0 ? NM : 1];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int i = 0; i < (NS > 0 ? NS : 1); ++i) s[i] = 0.0;
+#pragma unroll
+        for (int i = 0; i < (NM > 0 ? NM : 1); ++i) m[i] = 0.0;
+    }
+};
+
+// Reduce red over the CTA; thread 0 returns the CTA total in red.
+template <int NS, int NM>
+__device__ __forceinline__ void block_reduce(Red<NS, NM> &red) {
+    constexpr int NR = NS + NM;
+    __shared__ double sred[kWarps][NR > 0 ? NR : 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+        double v = red.s[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) sred[warp][i] = v;
+    }
+#pragma unroll
+    for (int i = 0; i < NM; ++i) {
+        double v = red.m[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = nanmax(v, __shfl_down_sync(0xffffffffu, v, o));
+        if (lane == 0) sred[warp][NS + i] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            double a = 0.0;
+            for (int w = 0; w < kWarps; ++w) a += sred[w][i];
+            red.s[i] = a;
+        }
+#pragma unroll
+        for (int i = 0; i < NM; ++i) {
+            double a = 0.0;
+            for (int w = 0; w < kWarps; ++w) a = nanmax(a, sred[w][NS + i]);
+            red.m[i] = a;
+        }
+    }
+    __syncthreads();
+}
+
+// Per-CTA partials -> the last CTA to arrive sums them in CTA order and
+// calls fin(total) with every thread of that CTA (thread 0 holds nothing
+// special; the total is broadcast through shared memory).
+template <int NS, int NM, class Fin>
+__device__ __forceinline__ void grid_finish(Red<NS, NM> &red, double *partials, unsigned int *ticket,
+                                            Fin &fin) {
+    constexpr int NR = NS + NM;
+    __shared__ bool am_last;
+    __shared__ double total[NR > 0 ? NR : 1];
+    block_reduce<NS, NM>(red);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < NS; ++i) partials[(size_t)blockIdx.x * NR + i] = red.s[i];
+#pragma unroll
+        for (int i = 0; i < NM; ++i) partials[(size_t)blockIdx.x * NR + NS + i] = red.m[i];
+        __threadfence();
+        unsigned int t = atomicAdd(ticket, 1u);
+        am_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    Red<NS, NM> acc;
+    acc.zero();
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < NS; ++i) acc.s[i] += __ldcg(partials + (size_t)b * NR + i);
+#pragma unroll
+        for (int i = 0; i < NM; ++i) acc.m[i] = nanmax(acc.m[i], __ldcg(partials + (size_t)b * NR + NS + i));
+    }
+    block_reduce<NS, NM>(acc);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < NS; ++i) total[i] = acc.s[i];
+#pragma unroll
+        for (int i = 0; i < NM; ++i) total[NS + i] = acc.m[i];
+        *ticket = 0u;
+    }
+    __syncthreads();
+    Red<NS, NM> tot;
+#pragma unroll
+    for (int i = 0; i < NS; ++i) tot.s[i] = total[i];
+#pragma unroll
+    for (int i = 0; i < NM; ++i) tot.m[i] = total[NS + i];
+    fin(tot);
+}
+
+// ------------------------------------------------------ row-block SpMV core
+
+// Row reduction of one block item with lane groups of G threads.  sprod
+// holds the item's products; epi.row(r, s1, s2, red) consumes each row.
+template <int G, bool SPLIT, class Acc, class T, class Epi, class RedT>
+__device__ __forceinline__ void reduce_rows(const CsrDev<T> &M, const Item &it, const Acc *sprod, Epi &epi,
+                                            RedT &red) {
+    const int lane_g = threadIdx.x & (G - 1);
+    const int grp = threadIdx.x / G;
+    constexpr int ngrp = kThreads / G;
+    const int R = it.r1 - it.r0;
+    for (int base = 0; base < R; base += ngrp) {
+        const int r = it.r0 + base + grp;
+        const bool active = (base + grp) < R;
+        Acc s1 = Acc(0), s2 = Acc(0);
+        if (active) {
+            const int a = __ldg(M.rowptr + r) - it.k0;
+            const int b = __ldg(M.rowptr + r + 1) - it.k0;
+            if (SPLIT) {
+                const int sp = __ldg(M.pend + r) - it.k0;
+                for (int e = a + lane_g; e < b; e += G) {
+                    if (e < sp) s1 += sprod[e]; else s2 += sprod[e];
+                }
+            } else {
+                for (int e = a + lane_g; e < b; e += G) s1 += sprod[e];
+            }
+        }
+        if (G > 1) {
+#pragma unroll
+            for (int o = G / 2; o > 0; o >>= 1) {
+                s1 += __shfl_down_sync(0xffffffffu, s1, o, G);
+                if (SPLIT) s2 += __shfl_down_sync(0xffffffffu, s2, o, G);
+            }
+        }
+        if (active && lane_g == 0) epi.row(r, s1, s2, red);
+    }
+}
+
+// Process every item assigned to this CTA (items blockIdx.x, +gridDim.x, ...).
+// gather(c) returns the vector entry for column c in the accumulation type.
+template <class Acc, bool SPLIT, class T, class Gather, class Epi, class RedT>
+__device__ __forceinline__ void run_items(const CsrDev<T> &M, const Gather &gather, Epi &epi, RedT &red) {
+    __shared__ Acc sprod[kCap];
+    __shared__ bool last_piece;
+    __shared__ Acc wsum[2][kWarps];
+    for (int itx = blockIdx.x; itx < M.nitems; itx += gridDim.x) {
+        const Item it = M.items[itx];
+        const int nnz = it.k1 - it.k0;
+        if (it.r1 >= 0) {
+            T v[kPerThread];
+            int c[kPerThread];
+#pragma unroll
+            for (int u = 0; u < kPerThread; ++u) {
+                const int e = u * kThreads + threadIdx.x;
+                if (e < nnz) {
+                    v[u] = __ldg(M.val + it.k0 + e);
+                    c[u] = __ldg(M.col + it.k0 + e);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kPerThread; ++u) {
+                const int e = u * kThreads + threadIdx.x;
+                if (e < nnz) sprod[e] = Acc(v[u]) * gather(c[u]);
+            }
+            __syncthreads();
+            const int R = it.r1 - it.r0;
+            const int avg = R > 0 ? nnz / R : 0;
+            if (avg >= 24) reduce_rows<32, SPLIT, Acc>(M, it, sprod, epi, red);
+            else if (avg >= 12) reduce_rows<16, SPLIT, Acc>(M, it, sprod, epi, red);
+            else if (avg >= 6) reduce_rows<8, SPLIT, Acc>(M, it, sprod, epi, red);
+            else if (avg >= 3) reduce_rows<4, SPLIT, Acc>(M, it, sprod, epi, red);
+            else reduce_rows<1, SPLIT, Acc>(M, it, sprod, epi, red);
+            __syncthreads();
+        } else {
+            // piece of a long row
+            const int row = it.r0;
+            const int lr = -(it.r1 + 1);
+            const int sp = SPLIT ? __ldg(M.pend + row) : 0x7fffffff;
+            Acc s1 = Acc(0), s2 = Acc(0);
+            for (int base = it.k0; base < it.k1; base += kCap) {
+                T v[kPerThread];
+                int c[kPerThread];
+#pragma unroll
+                for (int u = 0; u < kPerThread; ++u) {
+                    const int k = base + u * kThreads + threadIdx.x;
+                    if (k < it.k1) {
+                        v[u] = __ldg(M.val + k);
+                        c[u] = __ldg(M.col + k);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kPerThread; ++u) {
+                    const int k = base + u * kThreads + threadIdx.x;
+                    if (k < it.k1) {
+                        const Acc pr = Acc(v[u]) * gather(c[u]);
+                        if (!SPLIT || k < sp) s1 += pr; else s2 += pr;
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                s1 += __shfl_down_sync(0xffffffffu, s1, o);
+                s2 += __shfl_down_sync(0xffffffffu, s2, o);
+            }
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+            if (lane == 0) { wsum[0][warp] = s1; wsum[1][warp] = s2; }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double a1 = 0.0, a2 = 0.0;
+                for (int w = 0; w < kWarps; ++w) { a1 += (double)wsum[0][w]; a2 += (double)wsum[1][w]; }
+                M.lr_part[2 * (size_t)itx] = a1;
+                M.lr_part[2 * (size_t)itx + 1] = a2;
+                __threadfence();
+                const LongRow L = M.longrows[lr];
+                const int t = atomicAdd(M.lr_count + lr, 1);
+                last_piece = (t == L.npieces - 1);
+                if (last_piece) {
+                    __threadfence();
+                    double t1 = 0.0, t2 = 0.0;
+                    for (int p = 0; p < L.npieces; ++p) {
+                        t1 += __ldcg(M.lr_part + 2 * (size_t)(L.first_item + p));
+                        t2 += __ldcg(M.lr_part + 2 * (size_t)(L.first_item + p) + 1);
+                    }
+                    M.lr_count[lr] = 0;
+                    epi.row(row, Acc(t1), Acc(t2), red);
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// ------------------------------------------------------------- utilities
+
+// Kernel launches issued by this host thread (for the launch count the
+// library reports; CUDA graph executions are counted from the solve's
+// iteration counters instead).
+extern thread_local long long g_launches;
+
+// Launch kern<<<grid, block, 0, stream>>>(args...) and count it.
+template <class... KArgs, class... Args>
+inline void launch(void (*kern)(KArgs...), int grid, int block, cudaStream_t stream, Args &&...args) {
+    std::tuple<KArgs...> vals(std::forward<Args>(args)...);
+    void *ptrs[sizeof...(KArgs) > 0 ? sizeof...(KArgs) : 1];
+    std::apply([&](auto &...e) {
+        int i = 0;
+        ((ptrs[i++] = (void *)&e), ...);
+    }, vals);
+    ++g_launches;
+    GB_CUDA(cudaLaunchKernel((const void *)kern, dim3(grid > 0 ? grid : 1), dim3(block), ptrs, 0, stream));
+}
+
+__host__ __device__ __forceinline__ int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+int device_sm_count();
+int grid_for_items(int nitems, const void *kernel, int smem_dynamic = 0);
+int grid_for_n(long long n, int threads = kThreads);
+
+}  // namespace gb

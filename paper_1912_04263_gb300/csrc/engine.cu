@@ -1,0 +1,1190 @@
+// Solve engine: ADMM (Algorithm 1) with the reduced KKT system eq.
+// (kkt_red_sc) solved by warm-started Jacobi-PCG (Algorithm 3,
+// Section 5.3), on the equilibrated problem, in working precision T
+// (float: FP32 matrices and vectors with FP64 dot products and FP64
+// termination reductions; double: everything FP64).
+//
+// Data layout in device memory (T unless noted):
+//   A      m x n CSR          PAt = [P A'] n x (n+m) CSR, pend splits P | A'
+//   xy  = [x ; y]    (n+m)    ADMM primal x and dual y, contiguous so that
+//                             one gather over PAt reads P x and A' y
+//   xt  = [x~ ; t0]  (n+m)    PCG iterate x~ (the warm start) and
+//                             t0 = rho (A x~ - z) + y for the next PCG init
+//   pt  = [p ; t]    (n+m)    PCG direction p and t = rho A p
+//   z, zt (= A x~), l, u (m); q, minv, diagP, colsq, pc (previous p),
+//   kp (K p), r, yv (= M^{-1} r) (n); D, E (double) for unscaling.
+//
+// Kernels of one ADMM iteration (each row-block kernel streams one matrix):
+//   pcg_init   PAt: r = P x~ + sigma (x~ - x) + q + A' t0  (= K x~ - b),
+//              yv = M^{-1} r, r'yv, ||r||_inf          [Alg. 3 initialize]
+//   pcg_p_t    A:   p = -yv + beta p_prev, t = rho A p [Alg. 3 direction;
+//                                                        K-apply, part 1]
+//   pcg_kp     PAt: Kp = P p + sigma p + A' t, p'Kp    [K-apply, part 2]
+//   pcg_update n:   x~ += a p, r += a Kp, yv = M^{-1} r, r'yv, ||r||_inf,
+//                   beta, stop test ||r||_inf <= eps  [Alg. 3 loop body]
+//   admm_update A:  z~ = A x~; x, z (projection), y (dual), t0
+//                                                   [Alg. 1 steps 5-7]
+// every check_every iterations:
+//   check_a    A:   ||A x - z||, ||A x||, ||z|| (FP64 accumulation)
+//   check_b    PAt: ||P x + q + A'y||, ||P x||, ||A'y||, objective; then
+//              eq. (termination), the PCG tolerance of Section 5.3.4 and
+//              the rho update (Section 3.4 / 5.3.3 or the learned policy)
+//   rho_apply  n, m: M^{-1} and t0 for a changed rho
+#include <math.h>
+
+#include <algorithm>
+#include <cstddef>
+#include <initializer_list>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <tuple>
+#include <utility>
+
+#include "common.cuh"
+#include "engine.cuh"
+#include "policy.cuh"
+
+namespace gb {
+
+namespace {
+
+template <class T>
+struct Vecs {
+    T *xy, *xt, *pt;
+    T *z, *zt, *l, *u;
+    T *q, *minv, *diagp, *colsq, *pc, *kp, *r, *yv;
+    const double *D, *E;
+    double *x_out, *y_out, *z_out;
+    int n, m;
+};
+
+// resident CTAs per SM requested for the row-block kernels of the PCG loop
+// (bounds registers so that enough loads are in flight per SM)
+#ifndef GB_MIN_BLOCKS
+#define GB_MIN_BLOCKS 4
+#endif
+constexpr int kMinBlocks = GB_MIN_BLOCKS;
+
+template <class T>
+__device__ __forceinline__ T clampv(T v, T lo, T hi) {
+    return v < lo ? lo : (v > hi ? hi : v);
+}
+
+// ------------------------------------------------------------ gathers
+
+template <class T, class Acc>
+struct GatherVec {
+    const T *v;
+    __device__ __forceinline__ Acc operator()(int c) const { return Acc(__ldg(v + c)); }
+};
+
+template <class T>
+struct GatherDir {  // p = -yv + beta * p_prev
+    const T *yv, *pc;
+    T beta;
+    __device__ __forceinline__ T operator()(int c) const { return -__ldg(yv + c) + beta * __ldg(pc + c); }
+};
+
+// ------------------------------------------------------------ kernels
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_reset(Vecs<T> v, Status *st, cudaGraphConditionalHandle hA,
+                                                    int use_h) {
+    const int n = v.n, m = v.m;
+    const bool warm = st->warm != 0;
+    const double rho = warm ? st->rho : st->rho0;
+    const double sigma = st->sigma;
+    const long long N = n > m ? n : m;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        if (i < n) {
+            if (!warm) {
+                v.xy[i] = T(0);
+                v.xt[i] = T(0);
+            }
+            v.minv[i] = T(1.0 / ((double)v.diagp[i] + sigma + rho * (double)v.colsq[i]));
+            v.pc[i] = T(0);
+        }
+        if (i < m && !warm) {
+            v.xy[n + i] = T(0);
+            v.xt[n + i] = T(0);
+            v.z[i] = T(0);
+            v.zt[i] = T(0);
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->rho = rho;
+        st->k = 0;
+        st->cg_total = 0;
+        st->status = 0;
+        st->eps_pcg = st->eps0;
+        st->rho_updates = 0;
+        st->rho_changed = 0;
+        st->fallbacks = 0;
+        st->stall_count = 0;
+        st->stall_left = 0;
+        st->policy_disabled = 0;
+        st->last_merit = -1.0;
+        st->prev_merit = -1.0;
+        st->cg_since_update = 0;
+        st->admm_continue = st->max_iter > 0 ? 1 : 0;
+        if (use_h) cudaGraphSetConditional(hA, st->admm_continue);
+    }
+}
+
+// r = K x~ - b = P x~ + sigma (x~ - x) + q + A' t0,  yv = M^{-1} r
+template <class T>
+struct EpiInit {
+    Vecs<T> v;
+    T sigma;
+    __device__ __forceinline__ void row(int i, T s1, T, Red<1, 1> &red) {
+        const T r = s1 + sigma * (v.xt[i] - v.xy[i]) + v.q[i];
+        const T y = v.minv[i] * r;
+        v.r[i] = r;
+        v.yv[i] = y;
+        v.pc[i] = T(0);
+        red.s[0] += (double)r * (double)y;
+        red.m[0] = nanmax(red.m[0], fabs((double)r));
+    }
+};
+
+template <class T>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_pcg_init(CsrDev<T> PAt, Vecs<T> v, Status *st, double *partials,
+                                                       cudaGraphConditionalHandle hP, int use_h) {
+    EpiInit<T> epi{v, T(st->sigma)};
+    Red<1, 1> red;
+    red.zero();
+    run_items<T, false>(PAt, GatherVec<T, T>{v.xt}, epi, red);
+    auto fin = [&](const Red<1, 1> &t) {
+        if (threadIdx.x != 0) return;
+        st->ry = t.s[0];
+        st->rnorm = t.m[0];
+        st->beta = 0.0;
+        st->cg_it = 0;
+        st->breakdown = 0;
+        const int cont = (isfinite(t.m[0]) && t.m[0] > st->eps_pcg && st->max_cg > 0) ? 1 : 0;
+        st->pcg_continue = cont;
+        if (use_h) cudaGraphSetConditional(hP, cont);
+    };
+    grid_finish<1, 1>(red, partials, &st->tickets[kTkI1], fin);
+}
+
+// p = -yv + beta p_prev (stored in pt[0..n)), t = rho A p (pt[n..n+m))
+template <class T>
+struct EpiDir {
+    T *t;
+    T rho;
+    __device__ __forceinline__ void row(int j, T s1, T, Red<0, 0> &) { t[j] = rho * s1; }
+};
+
+template <class T>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_pcg_p_t(CsrDev<T> A, Vecs<T> v, const Status *st) {
+    const T beta = T(st->beta);
+    const int n = v.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        v.pt[i] = -v.yv[i] + beta * v.pc[i];
+    EpiDir<T> epi{v.pt + n, T(st->rho)};
+    Red<0, 0> red;
+    run_items<T, false>(A, GatherDir<T>{v.yv, v.pc, beta}, epi, red);
+}
+
+// Kp = P p + sigma p + A' t;  p'Kp
+template <class T>
+struct EpiKp {
+    Vecs<T> v;
+    T sigma;
+    __device__ __forceinline__ void row(int i, T s1, T, Red<1, 0> &red) {
+        const T p = v.pt[i];
+        const T kp = s1 + sigma * p;
+        v.kp[i] = kp;
+        red.s[0] += (double)p * (double)kp;
+    }
+};
+
+template <class T>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_pcg_kp(CsrDev<T> PAt, Vecs<T> v, Status *st, double *partials) {
+    EpiKp<T> epi{v, T(st->sigma)};
+    Red<1, 0> red;
+    red.zero();
+    run_items<T, false>(PAt, GatherVec<T, T>{v.pt}, epi, red);
+    auto fin = [&](const Red<1, 0> &t) {
+        if (threadIdx.x != 0) return;
+        const double pkp = t.s[0];
+        st->pkp = pkp;
+        if (pkp > 0.0 && isfinite(pkp)) {
+            st->alpha_cg = st->ry / pkp;  // step length alpha = r'y / p'Kp
+        } else {
+            st->alpha_cg = 0.0;
+            st->breakdown = 1;
+        }
+    };
+    grid_finish<1, 0>(red, partials, &st->tickets[kTkK2], fin);
+}
+
+// x~ += a p; r += a Kp; yv = M^{-1} r; p_prev = p; r'yv; ||r||_inf; beta
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_pcg_update(Vecs<T> v, Status *st, double *partials,
+                                                         cudaGraphConditionalHandle hP, int use_h) {
+    const double a = st->alpha_cg;
+    const int n = v.n;
+    Red<1, 1> red;
+    red.zero();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const T p = v.pt[i];
+        const T x = T((double)v.xt[i] + a * (double)p);
+        const T r = T((double)v.r[i] + a * (double)v.kp[i]);
+        const T y = v.minv[i] * r;
+        v.xt[i] = x;
+        v.r[i] = r;
+        v.yv[i] = y;
+        v.pc[i] = p;
+        red.s[0] += (double)r * (double)y;
+        red.m[0] = nanmax(red.m[0], fabs((double)r));
+    }
+    auto fin = [&](const Red<1, 1> &t) {
+        if (threadIdx.x != 0) return;
+        const double ry_new = t.s[0];
+        st->beta = st->ry != 0.0 ? ry_new / st->ry : 0.0;
+        st->ry = ry_new;
+        st->rnorm = t.m[0];
+        st->cg_it += 1;
+        st->cg_total += 1;
+        const int cont = (!st->breakdown && isfinite(t.m[0]) && t.m[0] > st->eps_pcg && st->cg_it < st->max_cg) ? 1 : 0;
+        st->pcg_continue = cont;
+        if (use_h) cudaGraphSetConditional(hP, cont);
+    };
+    grid_finish<1, 1>(red, partials, &st->tickets[kTkK3], fin);
+}
+
+// z~ = A x~;  relaxation, projection, dual update (Algorithm 1 steps 5-7);
+// t0 = rho (z~ - z) + y for the next PCG initialisation
+template <class T>
+struct EpiAdmm {
+    Vecs<T> v;
+    T alpha, rho, rho_inv;
+    __device__ __forceinline__ void row(int j, T s1, T, Red<0, 0> &) {
+        const int n = v.n;
+        const T zt = s1;
+        const T zr = alpha * zt + (T(1) - alpha) * v.z[j];
+        const T y = v.xy[n + j];
+        const T zn = clampv(zr + y * rho_inv, v.l[j], v.u[j]);
+        const T yn = y + rho * (zr - zn);
+        v.z[j] = zn;
+        v.zt[j] = zt;
+        v.xy[n + j] = yn;
+        v.xt[n + j] = rho * (zt - zn) + yn;
+    }
+};
+
+template <class T>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_admm_update(CsrDev<T> A, Vecs<T> v, Status *st) {
+    const T alpha = T(st->alpha);
+    const T rho = T(st->rho);
+    const int n = v.n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        v.xy[i] = alpha * v.xt[i] + (T(1) - alpha) * v.xy[i];
+    EpiAdmm<T> epi{v, alpha, rho, T(1.0 / st->rho)};
+    Red<0, 0> red;
+    run_items<T, false>(A, GatherVec<T, T>{v.xt}, epi, red);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->k += 1;
+        st->cg_since_update += st->cg_it;
+    }
+}
+
+// Termination check, part A (rows of A): r_prim = A x - z, FP64 sums.
+template <class T>
+struct EpiCheckA {
+    Vecs<T> v;
+    __device__ __forceinline__ void row(int j, double s1, double, Red<0, 6> &red) {
+        const double z = (double)v.z[j];
+        const double rp = s1 - z;
+        const double e = v.E[j];
+        red.m[0] = nanmax(red.m[0], fabs(rp));
+        red.m[1] = nanmax(red.m[1], fabs(s1));
+        red.m[2] = nanmax(red.m[2], fabs(z));
+        red.m[3] = nanmax(red.m[3], fabs(rp) / e);
+        red.m[4] = nanmax(red.m[4], fabs(s1) / e);
+        red.m[5] = nanmax(red.m[5], fabs(z) / e);
+    }
+};
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_check_a(CsrDev<T> A, Vecs<T> v, Status *st, double *partials) {
+    EpiCheckA<T> epi{v};
+    Red<0, 6> red;
+    red.zero();
+    run_items<double, false>(A, GatherVec<T, double>{v.xy}, epi, red);
+    auto fin = [&](const Red<0, 6> &t) {
+        if (threadIdx.x == 0)
+            for (int i = 0; i < 6; ++i) st->c1[i] = t.m[i];
+    };
+    grid_finish<0, 6>(red, partials, &st->tickets[kTkC1], fin);
+}
+
+// Part B (rows of [P A']): r_dual = P x + q + A'y, FP64 sums; objective.
+template <class T>
+struct EpiCheckB {
+    Vecs<T> v;
+    __device__ __forceinline__ void row(int i, double px, double aty, Red<1, 6> &red) {
+        const double q = (double)v.q[i];
+        const double rd = px + q + aty;
+        const double d = v.D[i];
+        red.m[0] = nanmax(red.m[0], fabs(rd));
+        red.m[1] = nanmax(red.m[1], fabs(px));
+        red.m[2] = nanmax(red.m[2], fabs(aty));
+        red.m[3] = nanmax(red.m[3], fabs(rd) / d);
+        red.m[4] = nanmax(red.m[4], fabs(px) / d);
+        red.m[5] = nanmax(red.m[5], fabs(aty) / d);
+        red.s[0] += (double)v.xy[i] * (0.5 * px + q);
+    }
+};
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_check_b(CsrDev<T> PAt, Vecs<T> v, Status *st, double *partials,
+                                                      PolicyDev pol, cudaGraphConditionalHandle hA, int use_h) {
+    __shared__ double new_rho_sh;
+    __shared__ int decide_sh;
+    EpiCheckB<T> epi{v};
+    Red<1, 6> red;
+    red.zero();
+    run_items<double, true>(PAt, GatherVec<T, double>{v.xy}, epi, red);
+    auto fin = [&](const Red<1, 6> &t) {
+        if (threadIdx.x == 0) {
+            const double cinv = st->cinv;
+            st->r_prim = st->c1[kC1RpU];
+            st->r_dual = t.m[3] * cinv;
+            st->eps_prim = st->eps_abs + st->eps_rel * fmax(st->c1[kC1AxU], st->c1[kC1ZU]);
+            st->eps_dual = st->eps_abs + st->eps_rel * cinv * fmax(fmax(t.m[4], t.m[5]), st->qnorm_u);
+            st->rp_s = st->c1[kC1RpS];
+            st->ax_s = st->c1[kC1AxS];
+            st->z_s = st->c1[kC1ZS];
+            st->rd_s = t.m[0];
+            st->px_s = t.m[1];
+            st->aty_s = t.m[2];
+            st->obj = t.s[0] * cinv;
+            st->rho_changed = 0;
+            const bool finite = isfinite(st->r_prim) && isfinite(st->r_dual) && isfinite(st->rp_s) && isfinite(st->rd_s);
+            const bool conv = finite && st->r_prim <= st->eps_prim && st->r_dual <= st->eps_dual;
+            int status = 0;
+            if (!finite) status = GBOSQP_NONFINITE;
+            else if (conv) status = GBOSQP_SOLVED;
+            else if (st->k >= st->max_iter) status = GBOSQP_MAX_ITER;
+            st->status = status;
+            if (status == 0) {
+                st->eps_pcg = fmax(st->lambda * sqrt(st->rp_s * st->rd_s), st->eps_min);
+            }
+            decide_sh = (status == 0 && st->policy != GBOSQP_RHO_FIXED && st->rho_every > 0 &&
+                         st->k % st->rho_every == 0) ? 1 : 0;
+            new_rho_sh = st->rho;
+        }
+        __syncthreads();
+        if (decide_sh) {
+            if (st->policy == GBOSQP_RHO_LEARNED && pol.params != nullptr) {
+                policy_decide(pol, st, &new_rho_sh);  // whole CTA; falls back to the ratio rule
+            } else if (threadIdx.x == 0) {
+                new_rho_sh = rho_ratio(st);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (decide_sh) {
+                const double nr = new_rho_sh;
+                if (nr != st->rho && isfinite(nr) && nr > 0.0) {
+                    st->rho = nr;
+                    st->rho_changed = 1;
+                    st->rho_updates += 1;
+                }
+                st->cg_since_update = 0;
+            }
+            st->admm_continue = st->status == 0 ? 1 : 0;
+            if (use_h) cudaGraphSetConditional(hA, st->admm_continue);
+        }
+    };
+    grid_finish<1, 6>(red, partials, &st->tickets[kTkC2], fin);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_rho_apply(Vecs<T> v, const Status *st) {
+    if (!st->rho_changed) return;
+    const double rho = st->rho, sigma = st->sigma;
+    const int n = v.n, m = v.m;
+    const long long N = n > m ? n : m;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        if (i < n) v.minv[i] = T(1.0 / ((double)v.diagp[i] + sigma + rho * (double)v.colsq[i]));
+        if (i < m) v.xt[n + i] = T(rho) * (v.zt[i] - v.z[i]) + v.xy[n + i];
+    }
+}
+
+// Unscaled output: x = D x_bar, z = z_bar / E, y = E y_bar / c.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_output(Vecs<T> v, Status *st) {
+    const int n = v.n, m = v.m;
+    const double cinv = st->cinv;
+    const long long N = n > m ? n : m;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        if (i < n) v.x_out[i] = v.D[i] * (double)v.xy[i];
+        if (i < m) {
+            v.z_out[i] = (double)v.z[i] / v.E[i];
+            v.y_out[i] = v.E[i] * (double)v.xy[n + i] * cinv;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->warm = 0;
+}
+
+// Generic y = alpha M x (test hook and set-up helpers).
+template <class T, class Acc>
+struct EpiStore {
+    T *y;
+    Acc alpha;
+    __device__ __forceinline__ void row(int r, Acc s1, Acc s2, Red<0, 0> &) { y[r] = T(alpha * (s1 + s2)); }
+};
+
+template <class T, class Acc>
+__global__ void __launch_bounds__(kThreads) k_spmv(CsrDev<T> M, const T *x, T *y, Acc alpha) {
+    EpiStore<T, Acc> epi{y, alpha};
+    Red<0, 0> red;
+    run_items<Acc, false>(M, GatherVec<T, Acc>{x}, epi, red);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_spmv_dbl(CsrDev<T> M, const T *x, double *y) {
+    EpiStore<double, double> epi{y, 1.0};
+    Red<0, 0> red;
+    run_items<double, false>(M, GatherVec<T, double>{x}, epi, red);
+}
+
+// t0 = rho (zt - z) + y
+template <class T>
+__global__ void k_t0(Vecs<T> v, double rho) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < v.m) v.xt[v.n + j] = T(rho) * (v.zt[j] - v.z[j]) + v.xy[v.n + j];
+}
+
+template <class T>
+__global__ void k_minv(Vecs<T> v, double rho, double sigma) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < v.n) v.minv[i] = T(1.0 / ((double)v.diagp[i] + sigma + rho * (double)v.colsq[i]));
+}
+
+template <class T>
+__global__ void k_from_double(const double *in, T *out, long long n) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = T(in[i]);
+}
+
+template <class T>
+__global__ void k_to_double(const T *in, double *out, long long n) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (double)in[i];
+}
+
+template <class T>
+__global__ void k_neg(T *v, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = -v[i];
+}
+
+// Warm start: x_bar = x / D, y_bar = c y / E, z_bar = proj(A_bar x_bar).
+template <class T>
+__global__ void k_warm(Vecs<T> v, const double *x, const double *y, double c) {
+    const int n = v.n, m = v.m;
+    const long long N = n > m ? n : m;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+        if (i < n) {
+            const T xb = x ? T(x[i] / v.D[i]) : T(0);
+            v.xy[i] = xb;
+            v.xt[i] = xb;
+        }
+        if (i < m) v.xy[n + i] = y ? T(c * y[i] / v.E[i]) : T(0);
+    }
+}
+
+template <class T>
+__global__ void k_proj_z(Vecs<T> v) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < v.m) v.z[j] = clampv(v.zt[j], v.l[j], v.u[j]);
+}
+
+// ----------------------------------------------------- graph construction
+
+template <class... KArgs, class... Args>
+cudaGraphNode_t add_kernel(cudaGraph_t g, const cudaGraphNode_t *dep, void (*kern)(KArgs...), int grid,
+                           Args &&...args) {
+    std::tuple<KArgs...> vals(std::forward<Args>(args)...);
+    void *ptrs[sizeof...(KArgs)];
+    std::apply([&](auto &...e) {
+        int i = 0;
+        ((ptrs[i++] = (void *)&e), ...);
+    }, vals);
+    cudaKernelNodeParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.func = (void *)kern;
+    p.gridDim = dim3(grid > 0 ? grid : 1);
+    p.blockDim = dim3(kThreads);
+    p.sharedMemBytes = 0;
+    p.kernelParams = ptrs;
+    cudaGraphNode_t node;
+    GB_CUDA(cudaGraphAddKernelNode(&node, g, dep, dep ? 1 : 0, &p));
+    return node;
+}
+
+cudaGraphNode_t add_while(cudaGraph_t g, const cudaGraphNode_t *dep, cudaGraphConditionalHandle h,
+                          cudaGraph_t *body) {
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    GB_CUDA(cudaGraphAddNode(&node, g, dep, nullptr, dep ? 1 : 0, &cp));
+    *body = cp.conditional.phGraph_out[0];
+    return node;
+}
+
+// ------------------------------------------------------------------ engine
+
+template <class T>
+class Engine final : public EngineBase {
+public:
+    Engine(SetupData &&sd, const gbosqp_settings &s, cudaStream_t stream) : s_(s), stream_(stream) {
+        n = sd.n;
+        m = sd.m;
+        nnzA = sd.nnzA;
+        nnzPAt = sd.nnzPAt;
+        nnzP = sd.nnzP;
+        c_ = sd.c;
+        // matrices in working precision
+        A_rowptr_ = std::move(sd.A_rowptr);
+        A_col_ = std::move(sd.A_col);
+        PAt_rowptr_ = std::move(sd.PAt_rowptr);
+        PAt_col_ = std::move(sd.PAt_col);
+        PAt_pend_ = std::move(sd.PAt_pend);
+        A_val_ = convert(std::move(sd.A_val), nnzA);
+        PAt_val_ = convert(std::move(sd.PAt_val), nnzPAt);
+        D_ = std::move(sd.D);
+        E_ = std::move(sd.E);
+        // plans
+        build_plan_dev(sd.A_rowptr_host, planA_);
+        build_plan_dev(sd.PAt_rowptr_host, planPAt_);
+        // vectors
+        const size_t nm = (size_t)n + m;
+        xy_.alloc(sizeof(T) * std::max<size_t>(nm, 1));
+        xt_.alloc(sizeof(T) * std::max<size_t>(nm, 1));
+        pt_.alloc(sizeof(T) * std::max<size_t>(nm, 1));
+        for (DevBuf *b : {&z_, &zt_}) b->alloc(sizeof(T) * std::max(m, 1));
+        l_ = convert(std::move(sd.l), m);
+        u_ = convert(std::move(sd.u), m);
+        q_ = convert(std::move(sd.q), n);
+        diagp_ = convert(std::move(sd.diagP), n);
+        colsq_ = convert(std::move(sd.colsq), n);
+        for (DevBuf *b : {&minv_, &pc_, &kp_, &r_, &yv_, &tmp_n_}) b->alloc(sizeof(T) * std::max(n, 1));
+        tmp_nm_.alloc(sizeof(T) * std::max<size_t>(nm, 1));
+        x_out_.alloc(sizeof(double) * std::max(n, 1));
+        y_out_.alloc(sizeof(double) * std::max(m, 1));
+        z_out_.alloc(sizeof(double) * std::max(m, 1));
+        GB_CUDA(cudaMemsetAsync(xy_.p, 0, xy_.bytes, stream_));
+        GB_CUDA(cudaMemsetAsync(xt_.p, 0, xt_.bytes, stream_));
+        GB_CUDA(cudaMemsetAsync(z_.p, 0, z_.bytes, stream_));
+        GB_CUDA(cudaMemsetAsync(zt_.p, 0, zt_.bytes, stream_));
+        GB_CUDA(cudaMemsetAsync(x_out_.p, 0, x_out_.bytes, stream_));
+        GB_CUDA(cudaMemsetAsync(y_out_.p, 0, y_out_.bytes, stream_));
+        GB_CUDA(cudaMemsetAsync(z_out_.p, 0, z_out_.bytes, stream_));
+        // launch geometry and reduction scratch
+        // each kernel's grid: its items, capped at the CTAs that fit at once
+        gPt_ = grid_for_items(planA_.nitems, (const void *)k_pcg_p_t<T>);
+        gAdmm_ = grid_for_items(planA_.nitems, (const void *)k_admm_update<T>);
+        gCa_ = grid_for_items(planA_.nitems, (const void *)k_check_a<T>);
+        gKp_ = grid_for_items(planPAt_.nitems, (const void *)k_pcg_kp<T>);
+        gInit_ = grid_for_items(planPAt_.nitems, (const void *)k_pcg_init<T>);
+        gCb_ = grid_for_items(planPAt_.nitems, (const void *)k_check_b<T>);
+        gridN_ = std::max(1, std::min(grid_for_n(std::max(n, m)), device_sm_count() * 8));
+        const int maxgrid = std::max({gPt_, gAdmm_, gCa_, gKp_, gInit_, gCb_, gridN_});
+        partials_.alloc(sizeof(double) * (size_t)maxgrid * 8);
+        // status block
+        Status h;
+        std::memset(&h, 0, sizeof(h));
+        h.sigma = s.sigma;
+        h.alpha = s.alpha;
+        h.eps_abs = s.eps_abs;
+        h.eps_rel = s.eps_rel;
+        h.lambda = s.pcg_lambda;
+        h.eps_min = s.pcg_eps_min;
+        h.rho_min = s.rho_min;
+        h.rho_max = s.rho_max;
+        h.rho0 = s.rho0;
+        h.rho = s.rho0;
+        h.c = c_;
+        h.cinv = 1.0 / c_;
+        h.qnorm_s = sd.qnorm_s;
+        h.qnorm_u = sd.qnorm_u;
+        h.eps0 = std::max(s.pcg_lambda * sd.qnorm_s, s.pcg_eps_min);
+        h.eps_pcg = h.eps0;
+        h.n = n;
+        h.m = m;
+        const int ce = s.check_every;
+        h.max_iter = ((s.max_iter + ce - 1) / ce) * ce;
+        h.max_cg = s.max_cg_iter;
+        h.check_every = ce;
+        h.rho_every = s.rho_every;
+        h.policy = s.rho_policy;
+        st_.alloc(sizeof(Status));
+        st2_.alloc(sizeof(Status));
+        GB_CUDA(cudaMemcpyAsync(st_.p, &h, sizeof(h), cudaMemcpyHostToDevice, stream_));
+        // learned policy parameters
+        if (s.rho_policy == GBOSQP_RHO_LEARNED && s.policy_params) {
+            policy_.alloc(sizeof(float) * GBOSQP_POLICY_PARAMS);
+            GB_CUDA(cudaMemcpyAsync(policy_.p, s.policy_params, sizeof(float) * GBOSQP_POLICY_PARAMS,
+                                    cudaMemcpyHostToDevice, stream_));
+        }
+        GB_CUDA(cudaStreamSynchronize(stream_));
+        if (s.loop_mode == GBOSQP_LOOP_GRAPH) build_graph();
+    }
+
+    ~Engine() override {
+        if (exec_) cudaGraphExecDestroy(exec_);
+        if (graph_) cudaGraphDestroy(graph_);
+    }
+
+    // ---------------------------------------------------------- solve
+    int solve() override {
+        cudaEvent_t e0, e1;
+        GB_CUDA(cudaEventCreate(&e0));
+        GB_CUDA(cudaEventCreate(&e1));
+        GB_CUDA(cudaEventRecord(e0, stream_));
+        const long long before = g_launches;
+        if (exec_) {
+            GB_CUDA(cudaGraphLaunch(exec_, stream_));
+        } else {
+            host_solve();
+        }
+        GB_CUDA(cudaEventRecord(e1, stream_));
+        GB_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        GB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        solve_ms_ = ms;
+        Status h = read_status();
+        last_ = h;
+        solve_launches = g_launches - before;
+        if (exec_) {
+            // kernels executed by the graph: reset, output, per iteration
+            // pcg_init and admm_update, per PCG step three kernels, per
+            // check three kernels
+            const long long checks = s_.check_every > 0 ? h.k / s_.check_every : 0;
+            solve_launches += 2 + 2LL * h.k + 3LL * h.cg_total + 3LL * checks;
+        }
+        return h.status;
+    }
+
+    void update_rho(double rho) override {
+        // the next solve starts from rho; the preconditioner is rebuilt now
+        GB_CUDA(cudaMemcpyAsync((char *)st_.p + offsetof(Status, rho0), &rho, sizeof(double), cudaMemcpyHostToDevice,
+                                stream_));
+        GB_CUDA(cudaMemcpyAsync((char *)st_.p + offsetof(Status, rho), &rho, sizeof(double), cudaMemcpyHostToDevice,
+                                stream_));
+        launch(k_minv<T>, ceil_div(std::max(n, 1), 256), 256, stream_, vecs(), rho, s_.sigma);
+        GB_CUDA(cudaGetLastError());
+        GB_CUDA(cudaStreamSynchronize(stream_));
+    }
+
+    void warm_start(const double *x, const double *y) override {
+        DevBuf xd, yd;
+        if (x) {
+            xd.alloc(sizeof(double) * std::max(n, 1));
+            GB_CUDA(cudaMemcpyAsync(xd.p, x, sizeof(double) * n, cudaMemcpyHostToDevice, stream_));
+        }
+        if (y) {
+            yd.alloc(sizeof(double) * std::max(m, 1));
+            GB_CUDA(cudaMemcpyAsync(yd.p, y, sizeof(double) * m, cudaMemcpyHostToDevice, stream_));
+        }
+        Status h = read_status();
+        Vecs<T> v = vecs();
+        launch(k_warm<T>, gridN_, kThreads, stream_, v, xd.as<double>(), yd.as<double>(), c_);
+        spmv_dev(planA_, A_val_.as<T>(), v.xt, v.zt, T(1));
+        launch(k_proj_z<T>, ceil_div(std::max(m, 1), 256), 256, stream_, v);
+        launch(k_t0<T>, ceil_div(std::max(m, 1), 256), 256, stream_, v, h.rho0);
+        const int one = 1;
+        GB_CUDA(cudaMemcpyAsync((char *)st_.p + offsetof(Status, warm), &one, sizeof(int), cudaMemcpyHostToDevice,
+                                stream_));
+        GB_CUDA(cudaMemcpyAsync((char *)st_.p + offsetof(Status, rho), &h.rho0, sizeof(double), cudaMemcpyHostToDevice,
+                                stream_));
+        GB_CUDA(cudaGetLastError());
+        GB_CUDA(cudaStreamSynchronize(stream_));
+    }
+
+    void get_solution(double *x, double *y, double *z, bool device) override {
+        const cudaMemcpyKind k = device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        if (x && n) GB_CUDA(cudaMemcpyAsync(x, x_out_.p, sizeof(double) * n, k, stream_));
+        if (y && m) GB_CUDA(cudaMemcpyAsync(y, y_out_.p, sizeof(double) * m, k, stream_));
+        if (z && m) GB_CUDA(cudaMemcpyAsync(z, z_out_.p, sizeof(double) * m, k, stream_));
+        GB_CUDA(cudaStreamSynchronize(stream_));
+    }
+
+    void fill_info(gbosqp_info &info) override {
+        const Status &h = last_;
+        info.status = h.status;
+        info.iters = h.k;
+        info.pcg_iters = h.cg_total;
+        info.obj = h.obj;
+        info.r_prim = h.r_prim;
+        info.r_dual = h.r_dual;
+        info.eps_prim = h.eps_prim;
+        info.eps_dual = h.eps_dual;
+        info.rho = h.rho;
+        info.pcg_eps = h.eps_pcg;
+        info.solve_ms = solve_ms_;
+        info.rho_updates = h.rho_updates;
+        info.policy_fallbacks = h.fallbacks;
+        info.nnz_P = nnzP;
+        info.nnz_A = nnzA;
+    }
+
+    // ------------------------------------------------ inspection / steps
+    void get_scaling(double *D, double *E, double *c) override {
+        if (D && n) GB_CUDA(cudaMemcpyAsync(D, D_.p, sizeof(double) * n, cudaMemcpyDeviceToHost, stream_));
+        if (E && m) GB_CUDA(cudaMemcpyAsync(E, E_.p, sizeof(double) * m, cudaMemcpyDeviceToHost, stream_));
+        GB_CUDA(cudaStreamSynchronize(stream_));
+        if (c) *c = c_;
+    }
+
+    void get_scaled_csr(int which, int64_t *rowptr, int32_t *col, double *val) override {
+        const bool isA = which == GBOSQP_MAT_A;
+        const int nr = isA ? m : n;
+        const long long nnz = isA ? nnzA : nnzPAt;
+        const DevBuf &rp = isA ? A_rowptr_ : PAt_rowptr_;
+        const DevBuf &cl = isA ? A_col_ : PAt_col_;
+        const DevBuf &vl = isA ? A_val_ : PAt_val_;
+        if (rowptr) {
+            std::vector<int> tmp(nr + 1);
+            GB_CUDA(cudaMemcpyAsync(tmp.data(), rp.p, sizeof(int) * (nr + 1), cudaMemcpyDeviceToHost, stream_));
+            GB_CUDA(cudaStreamSynchronize(stream_));
+            for (int i = 0; i <= nr; ++i) rowptr[i] = tmp[i];
+        }
+        if (col && nnz) GB_CUDA(cudaMemcpyAsync(col, cl.p, sizeof(int) * nnz, cudaMemcpyDeviceToHost, stream_));
+        if (val && nnz) {
+            DevBuf d(sizeof(double) * nnz);
+            launch(k_to_double<T>, ceil_div(nnz, 256), 256, stream_, vl.as<T>(), d.as<double>(), nnz);
+            GB_CUDA(cudaMemcpyAsync(val, d.p, sizeof(double) * nnz, cudaMemcpyDeviceToHost, stream_));
+            GB_CUDA(cudaStreamSynchronize(stream_));
+        }
+        GB_CUDA(cudaStreamSynchronize(stream_));
+    }
+
+    void spmv(int which, const double *x, double *y, bool fp64acc) override {
+        const bool isA = which == GBOSQP_MAT_A;
+        const int nin = isA ? n : n + m;
+        const int nout = isA ? m : n;
+        DevBuf xd(sizeof(double) * std::max(nin, 1)), xT(sizeof(T) * std::max(nin, 1)), yT(sizeof(T) * std::max(nout, 1)),
+            yd(sizeof(double) * std::max(nout, 1));
+        if (nin) GB_CUDA(cudaMemcpyAsync(xd.p, x, sizeof(double) * nin, cudaMemcpyHostToDevice, stream_));
+        launch(k_from_double<T>, ceil_div(std::max(nin, 1), 256), 256, stream_, xd.as<double>(), xT.as<T>(), nin);
+        const DevPlan &pl = isA ? planA_ : planPAt_;
+        const T *val = isA ? A_val_.as<T>() : PAt_val_.as<T>();
+        if (fp64acc) {
+            // FP64 output through a double staging vector
+            DevBuf yy(sizeof(double) * std::max(nout, 1));
+            CsrDev<T> M = csr(pl, val);
+            const int g = grid_for_items(pl.nitems, (const void *)k_spmv_dbl<T>);
+            k_spmv_d(M, xT.as<T>(), yy.as<double>(), g);
+            GB_CUDA(cudaMemcpyAsync(y, yy.p, sizeof(double) * nout, cudaMemcpyDeviceToHost, stream_));
+        } else {
+            spmv_dev(pl, val, xT.as<T>(), yT.as<T>(), T(1));
+            launch(k_to_double<T>, ceil_div(std::max(nout, 1), 256), 256, stream_, yT.as<T>(), yd.as<double>(), nout);
+            GB_CUDA(cudaMemcpyAsync(y, yd.p, sizeof(double) * nout, cudaMemcpyDeviceToHost, stream_));
+        }
+        GB_CUDA(cudaGetLastError());
+        GB_CUDA(cudaStreamSynchronize(stream_));
+    }
+
+    void pcg(double rho, const double *b, const double *x0, double eps, int max_iter, double *x, int *iters,
+             double *rnorm) override {
+        // r0 = K x0 - b is formed by the PCG-init kernel with x = 0, q = -b,
+        // t0 = rho A x0, on private copies of the vectors it reads.
+        Vecs<T> v = vecs();
+        DevBuf xy(sizeof(T) * std::max(n + m, 1)), xt(sizeof(T) * std::max(n + m, 1)), q(sizeof(T) * std::max(n, 1)),
+            minv(sizeof(T) * std::max(n, 1)), bd(sizeof(double) * std::max(n, 1)), zt(sizeof(T) * std::max(m, 1)),
+            zz(sizeof(T) * std::max(m, 1));
+        GB_CUDA(cudaMemsetAsync(xy.p, 0, xy.bytes, stream_));
+        GB_CUDA(cudaMemsetAsync(zz.p, 0, zz.bytes, stream_));
+        GB_CUDA(cudaMemcpyAsync(bd.p, b, sizeof(double) * n, cudaMemcpyHostToDevice, stream_));
+        launch(k_from_double<T>, ceil_div(std::max(n, 1), 256), 256, stream_, bd.as<double>(), q.as<T>(), n);
+        launch(k_neg<T>, ceil_div(std::max(n, 1), 256), 256, stream_, q.as<T>(), n);
+        GB_CUDA(cudaMemcpyAsync(bd.p, x0, sizeof(double) * n, cudaMemcpyHostToDevice, stream_));
+        launch(k_from_double<T>, ceil_div(std::max(n, 1), 256), 256, stream_, bd.as<double>(), xt.as<T>(), n);
+        v.xy = xy.as<T>();
+        v.xt = xt.as<T>();
+        v.q = q.as<T>();
+        v.minv = minv.as<T>();
+        v.zt = zt.as<T>();
+        v.z = zz.as<T>();
+        spmv_dev(planA_, A_val_.as<T>(), v.xt, v.zt, T(1));
+        launch(k_t0<T>, ceil_div(std::max(m, 1), 256), 256, stream_, v, rho);
+        launch(k_minv<T>, ceil_div(std::max(n, 1), 256), 256, stream_, v, rho, s_.sigma);
+        // private status: parameters of the main one, with rho and eps set
+        Status h = read_status();
+        h.rho = rho;
+        h.eps_pcg = eps;
+        h.max_cg = max_iter;
+        std::memset(h.tickets, 0, sizeof(h.tickets));
+        GB_CUDA(cudaMemcpyAsync(st2_.p, &h, sizeof(h), cudaMemcpyHostToDevice, stream_));
+        Status *st = st2_.as<Status>();
+        launch_init(v, st, 0, 0);
+        int it = 0;
+        while (read_int(st2_, offsetof(Status, pcg_continue))) {
+            launch_step(v, st, 0, 0);
+            ++it;
+        }
+        Status r = read_status(st2_);
+        if (iters) *iters = r.cg_it;
+        if (rnorm) *rnorm = r.rnorm;
+        launch(k_to_double<T>, ceil_div(std::max(n, 1), 256), 256, stream_, v.xt, bd.as<double>(), n);
+        GB_CUDA(cudaMemcpyAsync(x, bd.p, sizeof(double) * n, cudaMemcpyDeviceToHost, stream_));
+        GB_CUDA(cudaStreamSynchronize(stream_));
+        (void)it;
+    }
+
+    void set_iterates(const double *x, const double *z, const double *y, const double *xt, double rho) override {
+        Vecs<T> v = vecs();
+        upload(x, v.xy, n);
+        upload(y, v.xy + n, m);
+        upload(z, v.z, m);
+        upload(xt, v.xt, n);
+        spmv_dev(planA_, A_val_.as<T>(), v.xt, v.zt, T(1));
+        launch(k_t0<T>, ceil_div(std::max(m, 1), 256), 256, stream_, v, rho);
+        launch(k_minv<T>, ceil_div(std::max(n, 1), 256), 256, stream_, v, rho, s_.sigma);
+        Status h = read_status();
+        h.rho = rho;
+        h.k = 0;
+        h.cg_total = 0;
+        h.status = 0;
+        h.rho_changed = 0;
+        h.cg_since_update = 0;
+        std::memset(h.tickets, 0, sizeof(h.tickets));
+        GB_CUDA(cudaMemcpyAsync(st_.p, &h, sizeof(h), cudaMemcpyHostToDevice, stream_));
+        GB_CUDA(cudaGetLastError());
+        GB_CUDA(cudaStreamSynchronize(stream_));
+    }
+
+    void get_iterates(double *x, double *z, double *y, double *xt, double *rho) override {
+        Vecs<T> v = vecs();
+        download(v.xy, x, n);
+        download(v.xy + n, y, m);
+        download(v.z, z, m);
+        download(v.xt, xt, n);
+        if (rho) *rho = read_status().rho;
+    }
+
+    int admm_iterations(int k, int *pcg_per_iter) override {
+        Vecs<T> v = vecs();
+        Status *st = st_.as<Status>();
+        int status = 0;
+        for (int it = 0; it < k; ++it) {
+            launch_init(v, st, 0, 0);
+            int cg = 0;
+            while (read_int(st_, offsetof(Status, pcg_continue))) {
+                launch_step(v, st, 0, 0);
+                ++cg;
+            }
+            if (pcg_per_iter) pcg_per_iter[it] = cg;
+            launch_admm(v, st);
+            const int kk = read_int(st_, offsetof(Status, k));
+            if (kk % s_.check_every == 0) {
+                launch_check(v, st, 0, 0);
+                launch_rho(v, st);
+                status = read_int(st_, offsetof(Status, status));
+                if (status != 0) break;
+            }
+        }
+        GB_CUDA(cudaStreamSynchronize(stream_));
+        last_ = read_status();
+        return status;
+    }
+
+    void check(double *out) override {
+        // evaluate on a private copy of the status so the solve state is kept
+        Status h = read_status();
+        h.policy = GBOSQP_RHO_FIXED;
+        std::memset(h.tickets, 0, sizeof(h.tickets));
+        GB_CUDA(cudaMemcpyAsync(st2_.p, &h, sizeof(h), cudaMemcpyHostToDevice, stream_));
+        Vecs<T> v = vecs();
+        launch_check(v, st2_.as<Status>(), 0, 0);
+        Status r = read_status(st2_);
+        const double vals[GBOSQP_CHECK_FIELDS] = {r.r_prim, r.r_dual, r.eps_prim, r.eps_dual, r.rp_s, r.rd_s,
+                                                  r.ax_s,   r.z_s,    r.px_s,     r.aty_s,    r.qnorm_s, r.obj,
+                                                  0.0,      0.0,      0.0,        0.0};
+        std::memcpy(out, vals, sizeof(vals));
+    }
+
+    double bench_kernel(int kernel, int reps) override {
+        Status h = read_status();
+        std::memset(h.tickets, 0, sizeof(h.tickets));
+        h.policy = GBOSQP_RHO_FIXED;
+        GB_CUDA(cudaMemcpyAsync(st2_.p, &h, sizeof(h), cudaMemcpyHostToDevice, stream_));
+        Status *st = st2_.as<Status>();
+        Vecs<T> v = vecs();
+        // the timed kernels read and write the solve's vectors; keep a copy
+        // of the state they modify and restore it afterwards
+        DevBuf save_xy(xy_.bytes), save_xt(xt_.bytes), save_z(z_.bytes), save_zt(zt_.bytes);
+        GB_CUDA(cudaMemcpyAsync(save_xy.p, xy_.p, xy_.bytes, cudaMemcpyDeviceToDevice, stream_));
+        GB_CUDA(cudaMemcpyAsync(save_xt.p, xt_.p, xt_.bytes, cudaMemcpyDeviceToDevice, stream_));
+        GB_CUDA(cudaMemcpyAsync(save_z.p, z_.p, z_.bytes, cudaMemcpyDeviceToDevice, stream_));
+        GB_CUDA(cudaMemcpyAsync(save_zt.p, zt_.p, zt_.bytes, cudaMemcpyDeviceToDevice, stream_));
+        auto one = [&]() {
+            switch (kernel) {
+                case GBOSQP_K_PCG_DIRECTION: launch(k_pcg_p_t<T>, gPt_, kThreads, stream_, csrA(), v, (const Status *)st); break;
+                case GBOSQP_K_PCG_KAPPLY: launch(k_pcg_kp<T>, gKp_, kThreads, stream_, csrPAt(), v, st, partials_.as<double>()); break;
+                case GBOSQP_K_PCG_UPDATE: launch(k_pcg_update<T>, gridN_, kThreads, stream_, v, st, partials_.as<double>(), (cudaGraphConditionalHandle)0, 0); break;
+                case GBOSQP_K_PCG_INIT: launch(k_pcg_init<T>, gInit_, kThreads, stream_, csrPAt(), v, st, partials_.as<double>(), (cudaGraphConditionalHandle)0, 0); break;
+                case GBOSQP_K_ADMM_UPDATE: launch(k_admm_update<T>, gAdmm_, kThreads, stream_, csrA(), v, st); break;
+                case GBOSQP_K_CHECK_A: launch(k_check_a<T>, gCa_, kThreads, stream_, csrA(), v, st, partials_.as<double>()); break;
+                case GBOSQP_K_CHECK_B: launch(k_check_b<T>, gCb_, kThreads, stream_, csrPAt(), v, st, partials_.as<double>(), policy(), (cudaGraphConditionalHandle)0, 0); break;
+                default: fail(GBOSQP_ERR_INVALID_ARG, "unknown kernel selector");
+            }
+        };
+        one();  // warm-up
+        cudaEvent_t e0, e1;
+        GB_CUDA(cudaEventCreate(&e0));
+        GB_CUDA(cudaEventCreate(&e1));
+        GB_CUDA(cudaEventRecord(e0, stream_));
+        for (int i = 0; i < reps; ++i) one();
+        GB_CUDA(cudaEventRecord(e1, stream_));
+        GB_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        GB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        GB_CUDA(cudaMemcpyAsync(xy_.p, save_xy.p, xy_.bytes, cudaMemcpyDeviceToDevice, stream_));
+        GB_CUDA(cudaMemcpyAsync(xt_.p, save_xt.p, xt_.bytes, cudaMemcpyDeviceToDevice, stream_));
+        GB_CUDA(cudaMemcpyAsync(z_.p, save_z.p, z_.bytes, cudaMemcpyDeviceToDevice, stream_));
+        GB_CUDA(cudaMemcpyAsync(zt_.p, save_zt.p, zt_.bytes, cudaMemcpyDeviceToDevice, stream_));
+        GB_CUDA(cudaStreamSynchronize(stream_));
+        return reps > 0 ? ms / reps : 0.0;
+    }
+
+private:
+    struct DevPlan {
+        DevBuf items, longrows, count, part;
+        int nitems = 0;
+        int nrows = 0;
+    };
+
+    DevBuf convert(DevBuf &&src, long long count) {
+        if (sizeof(T) == sizeof(double)) return std::move(src);
+        DevBuf out(sizeof(T) * std::max<long long>(count, 1));
+        if (count) launch(k_from_double<T>, ceil_div(count, 256), 256, stream_, src.as<double>(), out.as<T>(), count);
+        GB_CUDA(cudaGetLastError());
+        GB_CUDA(cudaStreamSynchronize(stream_));
+        return out;
+    }
+
+    void build_plan_dev(const std::vector<int> &rp, DevPlan &pl) {
+        HostPlan hp = build_plan(rp);
+        pl.nitems = (int)hp.items.size();
+        pl.nrows = (int)rp.size() - 1;
+        pl.items.alloc(sizeof(Item) * std::max<size_t>(hp.items.size(), 1));
+        pl.longrows.alloc(sizeof(LongRow) * std::max<size_t>(hp.longrows.size(), 1));
+        pl.count.alloc(sizeof(int) * std::max<size_t>(hp.longrows.size(), 1));
+        pl.part.alloc(sizeof(double) * 2 * std::max<size_t>(hp.items.size(), 1));
+        if (!hp.items.empty())
+            GB_CUDA(cudaMemcpyAsync(pl.items.p, hp.items.data(), sizeof(Item) * hp.items.size(), cudaMemcpyHostToDevice,
+                                    stream_));
+        if (!hp.longrows.empty())
+            GB_CUDA(cudaMemcpyAsync(pl.longrows.p, hp.longrows.data(), sizeof(LongRow) * hp.longrows.size(),
+                                    cudaMemcpyHostToDevice, stream_));
+        GB_CUDA(cudaMemsetAsync(pl.count.p, 0, pl.count.bytes, stream_));
+        GB_CUDA(cudaStreamSynchronize(stream_));
+    }
+
+    CsrDev<T> csr(const DevPlan &pl, const T *val) const {
+        const bool isA = &pl == &planA_;
+        CsrDev<T> M;
+        M.nrows = pl.nrows;
+        M.ncols = isA ? n : n + m;
+        M.rowptr = (isA ? A_rowptr_ : PAt_rowptr_).template as<int>();
+        M.col = (isA ? A_col_ : PAt_col_).template as<int>();
+        M.val = val;
+        M.pend = isA ? nullptr : PAt_pend_.template as<int>();
+        M.items = pl.items.template as<Item>();
+        M.nitems = pl.nitems;
+        M.longrows = pl.longrows.template as<LongRow>();
+        M.lr_count = pl.count.template as<int>();
+        M.lr_part = pl.part.template as<double>();
+        return M;
+    }
+    CsrDev<T> csrA() const { return csr(planA_, A_val_.as<T>()); }
+    CsrDev<T> csrPAt() const { return csr(planPAt_, PAt_val_.as<T>()); }
+
+    Vecs<T> vecs() const {
+        Vecs<T> v;
+        v.xy = xy_.as<T>();
+        v.xt = xt_.as<T>();
+        v.pt = pt_.as<T>();
+        v.z = z_.as<T>();
+        v.zt = zt_.as<T>();
+        v.l = l_.as<T>();
+        v.u = u_.as<T>();
+        v.q = q_.as<T>();
+        v.minv = minv_.as<T>();
+        v.diagp = diagp_.as<T>();
+        v.colsq = colsq_.as<T>();
+        v.pc = pc_.as<T>();
+        v.kp = kp_.as<T>();
+        v.r = r_.as<T>();
+        v.yv = yv_.as<T>();
+        v.D = D_.as<double>();
+        v.E = E_.as<double>();
+        v.x_out = x_out_.as<double>();
+        v.y_out = y_out_.as<double>();
+        v.z_out = z_out_.as<double>();
+        v.n = n;
+        v.m = m;
+        return v;
+    }
+
+    PolicyDev policy() const {
+        PolicyDev p;
+        p.params = policy_.as<float>();
+        return p;
+    }
+
+    void spmv_dev(const DevPlan &pl, const T *val, const T *x, T *y, T alpha) {
+        const int g = grid_for_items(pl.nitems, (const void *)k_spmv<T, T>);
+        launch(k_spmv<T, T>, g, kThreads, stream_, csr(pl, val), x, y, alpha);
+        GB_CUDA(cudaGetLastError());
+    }
+    void k_spmv_d(CsrDev<T> M, const T *x, double *y, int g) {
+        launch(k_spmv_dbl<T>, g, kThreads, stream_, M, x, y);
+        GB_CUDA(cudaGetLastError());
+    }
+
+    // ---- host-driven launches (same kernels as the graph)
+    void launch_init(const Vecs<T> &v, Status *st, cudaGraphConditionalHandle h, int use_h) {
+        launch(k_pcg_init<T>, gInit_, kThreads, stream_, csrPAt(), v, st, partials_.as<double>(), h, use_h);
+        GB_CUDA(cudaGetLastError());
+    }
+    void launch_step(const Vecs<T> &v, Status *st, cudaGraphConditionalHandle h, int use_h) {
+        launch(k_pcg_p_t<T>, gPt_, kThreads, stream_, csrA(), v, st);
+        launch(k_pcg_kp<T>, gKp_, kThreads, stream_, csrPAt(), v, st, partials_.as<double>());
+        launch(k_pcg_update<T>, gridN_, kThreads, stream_, v, st, partials_.as<double>(), h, use_h);
+        GB_CUDA(cudaGetLastError());
+    }
+    void launch_admm(const Vecs<T> &v, Status *st) {
+        launch(k_admm_update<T>, gAdmm_, kThreads, stream_, csrA(), v, st);
+        GB_CUDA(cudaGetLastError());
+    }
+    void launch_check(const Vecs<T> &v, Status *st, cudaGraphConditionalHandle h, int use_h) {
+        launch(k_check_a<T>, gCa_, kThreads, stream_, csrA(), v, st, partials_.as<double>());
+        launch(k_check_b<T>, gCb_, kThreads, stream_, csrPAt(), v, st, partials_.as<double>(), policy(), h, use_h);
+        GB_CUDA(cudaGetLastError());
+    }
+    void launch_rho(const Vecs<T> &v, Status *st) {
+        launch(k_rho_apply<T>, gridN_, kThreads, stream_, v, st);
+        GB_CUDA(cudaGetLastError());
+    }
+
+    void host_solve() {
+        Vecs<T> v = vecs();
+        Status *st = st_.as<Status>();
+        launch(k_reset<T>, gridN_, kThreads, stream_, v, st, 0, 0);
+        GB_CUDA(cudaGetLastError());
+        while (read_int(st_, offsetof(Status, admm_continue))) {
+            for (int s = 0; s < s_.check_every; ++s) {
+                launch_init(v, st, 0, 0);
+                while (read_int(st_, offsetof(Status, pcg_continue))) launch_step(v, st, 0, 0);
+                launch_admm(v, st);
+            }
+            launch_check(v, st, 0, 0);
+            launch_rho(v, st);
+        }
+        launch(k_output<T>, gridN_, kThreads, stream_, v, st);
+        GB_CUDA(cudaGetLastError());
+    }
+
+    // Whole solve as one graph:
+    //   reset -> WHILE(admm) { check_every x [pcg_init -> WHILE(pcg)
+    //   { p_t -> kp -> update } -> admm_update] -> check_a -> check_b
+    //   -> rho_apply } -> output
+    void build_graph() {
+        Vecs<T> v = vecs();
+        Status *st = st_.as<Status>();
+        double *part = partials_.as<double>();
+        CsrDev<T> A = csrA(), PAt = csrPAt();
+        GB_CUDA(cudaGraphCreate(&graph_, 0));
+        cudaGraphConditionalHandle hA;
+        GB_CUDA(cudaGraphConditionalHandleCreate(&hA, graph_, 1, cudaGraphCondAssignDefault));
+        cudaGraphNode_t n_reset = add_kernel(graph_, nullptr, k_reset<T>, gridN_, v, st, hA, 1);
+        cudaGraph_t body;
+        cudaGraphNode_t n_while = add_while(graph_, &n_reset, hA, &body);
+        add_kernel(graph_, &n_while, k_output<T>, gridN_, v, st);
+        cudaGraphNode_t prev = nullptr;
+        for (int s = 0; s < s_.check_every; ++s) {
+            cudaGraphConditionalHandle hP;
+            GB_CUDA(cudaGraphConditionalHandleCreate(&hP, body, 0, 0));
+            cudaGraphNode_t ni = add_kernel(body, prev ? &prev : nullptr, k_pcg_init<T>, gInit_, PAt, v, st, part, hP, 1);
+            cudaGraph_t pbody;
+            cudaGraphNode_t nw = add_while(body, &ni, hP, &pbody);
+            cudaGraphNode_t a = add_kernel(pbody, nullptr, k_pcg_p_t<T>, gPt_, A, v, (const Status *)st);
+            cudaGraphNode_t b = add_kernel(pbody, &a, k_pcg_kp<T>, gKp_, PAt, v, st, part);
+            add_kernel(pbody, &b, k_pcg_update<T>, gridN_, v, st, part, hP, 1);
+            prev = add_kernel(body, &nw, k_admm_update<T>, gAdmm_, A, v, st);
+        }
+        cudaGraphNode_t ca = add_kernel(body, &prev, k_check_a<T>, gCa_, A, v, st, part);
+        cudaGraphNode_t cb = add_kernel(body, &ca, k_check_b<T>, gCb_, PAt, v, st, part, policy(), hA, 1);
+        add_kernel(body, &cb, k_rho_apply<T>, gridN_, v, (const Status *)st);
+        GB_CUDA(cudaGraphInstantiate(&exec_, graph_, 0));
+    }
+
+    // ---- small host helpers
+    Status read_status() { return read_status(st_); }
+    Status read_status(const DevBuf &b) {
+        Status h;
+        GB_CUDA(cudaMemcpyAsync(&h, b.p, sizeof(h), cudaMemcpyDeviceToHost, stream_));
+        GB_CUDA(cudaStreamSynchronize(stream_));
+        return h;
+    }
+    int read_int(const DevBuf &b, size_t off) {
+        int v = 0;
+        GB_CUDA(cudaMemcpyAsync(&v, (const char *)b.p + off, sizeof(int), cudaMemcpyDeviceToHost, stream_));
+        GB_CUDA(cudaStreamSynchronize(stream_));
+        return v;
+    }
+    void upload(const double *src, T *dst, int count) {
+        if (!src || count <= 0) return;
+        DevBuf d(sizeof(double) * count);
+        GB_CUDA(cudaMemcpyAsync(d.p, src, sizeof(double) * count, cudaMemcpyHostToDevice, stream_));
+        launch(k_from_double<T>, ceil_div(count, 256), 256, stream_, d.as<double>(), dst, count);
+        GB_CUDA(cudaStreamSynchronize(stream_));
+    }
+    void download(const T *src, double *dst, int count) {
+        if (!dst || count <= 0) return;
+        DevBuf d(sizeof(double) * count);
+        launch(k_to_double<T>, ceil_div(count, 256), 256, stream_, src, d.as<double>(), count);
+        GB_CUDA(cudaMemcpyAsync(dst, d.p, sizeof(double) * count, cudaMemcpyDeviceToHost, stream_));
+        GB_CUDA(cudaStreamSynchronize(stream_));
+    }
+
+    gbosqp_settings s_;
+    cudaStream_t stream_;
+    double c_ = 1.0;
+    DevBuf A_rowptr_, A_col_, A_val_, PAt_rowptr_, PAt_col_, PAt_val_, PAt_pend_;
+    DevBuf D_, E_;
+    DevBuf xy_, xt_, pt_, z_, zt_, l_, u_, q_, minv_, diagp_, colsq_, pc_, kp_, r_, yv_, tmp_n_, tmp_nm_;
+    DevBuf x_out_, y_out_, z_out_;
+    DevBuf partials_, st_, st2_, policy_;
+    DevPlan planA_, planPAt_;
+    int gPt_ = 1, gAdmm_ = 1, gCa_ = 1, gKp_ = 1, gInit_ = 1, gCb_ = 1, gridN_ = 1;
+    cudaGraph_t graph_ = nullptr;
+    cudaGraphExec_t exec_ = nullptr;
+    float solve_ms_ = 0.f;
+    Status last_{};
+};
+
+}  // namespace
+
+std::unique_ptr<EngineBase> make_engine(SetupData &&sd, const gbosqp_settings &s, cudaStream_t stream) {
+    if (s.precision == GBOSQP_FP64) return std::unique_ptr<EngineBase>(new Engine<double>(std::move(sd), s, stream));
+    return std::unique_ptr<EngineBase>(new Engine<float>(std::move(sd), s, stream));
+}
+
+}  // namespace gb

@@ -1,0 +1,57 @@
+// Interfaces between device set-up (setup.cu), the per-precision solve
+// engine (engine.cu) and the C ABI (api.cu).
+#pragma once
+
+#include <memory>
+#include <vector>
+
+#include "common.cuh"
+
+namespace gb {
+
+// Output of device set-up: the equilibrated problem in FP64 on the device.
+struct SetupData {
+    int n = 0, m = 0;
+    long long nnzA = 0, nnzPAt = 0, nnzP = 0;
+    // A_bar (m x n) and [P_bar A_bar'] (n x (n+m)), CSR, int32 indices
+    DevBuf A_rowptr, A_col, A_val;
+    DevBuf PAt_rowptr, PAt_col, PAt_val, PAt_pend;
+    std::vector<int> A_rowptr_host, PAt_rowptr_host;
+    // vectors (double)
+    DevBuf q, l, u, D, E, diagP, colsq;
+    double c = 1.0;
+    double qnorm_s = 0.0;  // ||q_bar||_inf
+    double qnorm_u = 0.0;  // max_i |q_bar_i| / D_i  (times 1/c = ||q||_inf)
+};
+
+// Build SetupData from validated inputs (see osqp_setup).  Throws GbError.
+SetupData device_setup(const gbosqp_csr &P, const gbosqp_csr &A, const double *q, const double *l,
+                       const double *u, const gbosqp_settings &s, cudaStream_t stream);
+
+class EngineBase {
+public:
+    virtual ~EngineBase() = default;
+    virtual int solve() = 0;                                   // returns status
+    virtual void update_rho(double rho) = 0;
+    virtual void warm_start(const double *x, const double *y) = 0;
+    virtual void get_solution(double *x, double *y, double *z, bool device) = 0;
+    virtual void fill_info(gbosqp_info &info) = 0;
+    virtual void get_scaling(double *D, double *E, double *c) = 0;
+    virtual void get_scaled_csr(int which, int64_t *rowptr, int32_t *col, double *val) = 0;
+    virtual void spmv(int which, const double *x, double *y, bool fp64acc) = 0;
+    virtual void pcg(double rho, const double *b, const double *x0, double eps, int max_iter, double *x,
+                     int *iters, double *rnorm) = 0;
+    virtual void set_iterates(const double *x, const double *z, const double *y, const double *xt,
+                              double rho) = 0;
+    virtual void get_iterates(double *x, double *z, double *y, double *xt, double *rho) = 0;
+    virtual int admm_iterations(int k, int *pcg_per_iter) = 0;
+    virtual void check(double *out) = 0;
+    virtual double bench_kernel(int kernel, int reps) = 0;
+    int n = 0, m = 0;
+    long long solve_launches = 0;
+    long long nnzA = 0, nnzPAt = 0, nnzP = 0;
+};
+
+std::unique_ptr<EngineBase> make_engine(SetupData &&sd, const gbosqp_settings &s, cudaStream_t stream);
+
+}  // namespace gb

@@ -1,0 +1,730 @@
+// Device set-up of a QP (paper Section 5.2 "Representation of Matrices" and
+// Section 5.4 "Matrix Equilibration"):
+//   1. validation of the CSR inputs and bounds (device kernels, one flag word)
+//   2. A' in CSR by a stable LSD radix sort of A's nonzeros by column
+//      (so every row of A' is sorted), and the full P from its upper
+//      triangle as U'(strictly lower part) followed by U, row by row
+//   3. Ruiz equilibration, Algorithm 2, in FP64: column inf-norms of
+//      M = [[P, A'], [A, 0]] as row norms of P, A' and A (a segmented max
+//      over CSR rows, Section 5.4.1), the scaling delta = 1/sqrt(norm),
+//      pre- and post-multiplication of P, A and A' by diagonal matrices
+//      (Sections 5.4.2-5.4.3), and the cost scaling gamma
+//   4. the concatenated [P_bar A_bar'] (row i: row i of P_bar, then row i
+//      of A_bar' with columns offset by n), diag(P_bar) and the squared
+//      column norms of A_bar for the Jacobi preconditioner (Section 5.3.1)
+// Everything after the input copy stays on the device; the host reads one
+// validation word and the row pointers used to build the SpMV work plans.
+#include <math.h>
+
+#include <algorithm>
+#include <string>
+
+#include "common.cuh"
+#include "engine.cuh"
+
+namespace gb {
+
+namespace {
+
+constexpr int kScanBlock = 1024;
+constexpr int kRsWarps = 8;
+constexpr int kRsPerLane = 32;
+constexpr int kRsTile = 32 * kRsPerLane;
+
+enum Flag {
+    kFlagRowptr = 1,
+    kFlagColRange = 2,
+    kFlagColOrder = 4,
+    kFlagValue = 8,
+    kFlagLower = 16,
+    kFlagQ = 32,
+    kFlagBounds = 64,
+};
+
+// Stream-ordered temporary allocation.
+struct Tmp {
+    void *p = nullptr;
+    cudaStream_t s;
+    Tmp(size_t bytes, cudaStream_t st) : s(st) {
+        if (bytes == 0) bytes = 16;
+        cudaError_t e = cudaMallocAsync(&p, bytes, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            fail(GBOSQP_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+        }
+    }
+    ~Tmp() {
+        if (p) cudaFreeAsync(p, s);
+    }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+inline int blocks_for(long long n, int threads) { return (int)std::max(1LL, (n + threads - 1) / threads); }
+inline int warp_blocks(long long rows) { return (int)std::max(1LL, (rows + kWarps - 1) / kWarps); }
+
+// ------------------------------------------------------------ validation
+
+__global__ void k_check_rowptr(const int64_t *rp, int nrows, long long nnz, int *flags) {
+    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r == 0 && (rp[0] != 0 || rp[nrows] != nnz)) atomicOr(flags, kFlagRowptr);
+    if (r < nrows && rp[r + 1] < rp[r]) atomicOr(flags, kFlagRowptr);
+}
+
+__global__ void k_rowptr_i32(const int64_t *in, int n1, int *out) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n1) out[i] = (int)in[i];
+}
+
+// One warp per row: columns in range, strictly increasing, finite values,
+// and (upper) no entry below the diagonal.
+__global__ void k_check_rows(const int *rp, const int *col, const double *val, int nrows, int ncols,
+                             int upper, int *flags) {
+    const int row = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= nrows) return;
+    int bad = 0;
+    for (int k = rp[row] + lane; k < rp[row + 1]; k += 32) {
+        const int c = col[k];
+        if (c < 0 || c >= ncols) bad |= kFlagColRange;
+        if (k > rp[row] && col[k - 1] >= c) bad |= kFlagColOrder;
+        if (!isfinite(val[k])) bad |= kFlagValue;
+        if (upper && c < row) bad |= kFlagLower;
+    }
+    if (bad) atomicOr(flags, bad);
+}
+
+// Infinite-bound convention: |v| >= 1e20 is +-inf.
+__global__ void k_check_vectors(const double *q, int n, const double *l, const double *u, int m, double *qd,
+                                double *ld, double *ud, int *flags) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const double v = q[i];
+        if (!isfinite(v)) atomicOr(flags, kFlagQ);
+        qd[i] = v;
+    }
+    if (i < m) {
+        double a = l[i], b = u[i];
+        if (a != a || b != b || a > b) atomicOr(flags, kFlagBounds);
+        if (a <= -kInf) a = -INFINITY;
+        if (a >= kInf) a = INFINITY;
+        if (b >= kInf) b = INFINITY;
+        if (b <= -kInf) b = -INFINITY;
+        if (a == INFINITY || b == -INFINITY) atomicOr(flags, kFlagBounds);
+        ld[i] = a;
+        ud[i] = b;
+    }
+}
+
+// ----------------------------------------------------------------- scan
+
+__global__ void k_scan_block(const int *in, int n, int *out, int *bsum) {
+    __shared__ int wsum[32];
+    const int i = blockIdx.x * kScanBlock + threadIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int v = i < n ? in[i] : 0;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int s = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        wsum[lane] = s;
+    }
+    __syncthreads();
+    const int incl = x + (w > 0 ? wsum[w - 1] : 0);
+    if (i < n) out[i] = incl - v;
+    if (threadIdx.x == kScanBlock - 1) bsum[blockIdx.x] = incl;
+}
+
+__global__ void k_scan_add(int *out, int n, const int *boff) {
+    const int i = blockIdx.x * kScanBlock + threadIdx.x;
+    if (i < n) out[i] += boff[blockIdx.x];
+}
+
+__global__ void k_copy_int(int *dst, const int *src) { *dst = *src; }
+__global__ void k_zero_int(int *dst) { *dst = 0; }
+
+// out[0..n) = exclusive prefix sums of in, out[n] = total.
+void exclusive_scan(const int *in, int n, int *out, cudaStream_t st) {
+    if (n <= 0) {
+        launch(k_zero_int, 1, 1, st, out);
+        return;
+    }
+    const int nb = ceil_div(n, kScanBlock);
+    Tmp bsum((size_t)nb * sizeof(int), st);
+    launch(k_scan_block, nb, kScanBlock, st, in, n, out, bsum.as<int>());
+    if (nb == 1) {
+        launch(k_copy_int, 1, 1, st, out + n, bsum.as<int>());
+    } else {
+        Tmp boff((size_t)(nb + 1) * sizeof(int), st);
+        exclusive_scan(bsum.as<int>(), nb, boff.as<int>(), st);
+        launch(k_scan_add, nb, kScanBlock, st, out, n, boff.as<int>());
+        launch(k_copy_int, 1, 1, st, out + n, boff.as<int>() + nb);
+    }
+    GB_CUDA(cudaGetLastError());
+}
+
+// ------------------------------------------------------ radix sort by key
+
+__global__ void k_iota(int *v, long long n) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = (int)i;
+}
+
+__global__ void k_radix_hist(const int *keys, long long nnz, int shift, int ntiles, int *H) {
+    __shared__ int hist[kRsWarps][256];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tile = blockIdx.x * kRsWarps + w;
+    for (int d = lane; d < 256; d += 32) hist[w][d] = 0;
+    __syncwarp();
+    if (tile >= ntiles) return;
+    const long long base = (long long)tile * kRsTile;
+    for (int it = 0; it < kRsPerLane; ++it) {
+        const long long k = base + it * 32 + lane;
+        if (k < nnz) atomicAdd(&hist[w][(keys[k] >> shift) & 255], 1);
+    }
+    __syncwarp();
+    for (int d = lane; d < 256; d += 32) H[(size_t)d * ntiles + tile] = hist[w][d];
+}
+
+// Stable scatter: each warp walks its tile in order; equal digits within a
+// 32-key step are ranked by lane, and a per-warp running count per digit
+// carries the order across steps.
+__global__ void k_radix_scatter(const int *kin, const int *vin, long long nnz, int shift, int ntiles,
+                                const int *offs, int *kout, int *vout) {
+    __shared__ int cnt[kRsWarps][256];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tile = blockIdx.x * kRsWarps + w;
+    for (int d = lane; d < 256; d += 32) cnt[w][d] = 0;
+    __syncwarp();
+    if (tile >= ntiles) return;
+    const long long base = (long long)tile * kRsTile;
+    for (int it = 0; it < kRsPerLane; ++it) {
+        const long long k = base + it * 32 + lane;
+        const bool valid = k < nnz;
+        int key = 0, val = 0, d = 0;
+        if (valid) {
+            key = kin[k];
+            val = vin[k];
+            d = (key >> shift) & 255;
+        }
+        const unsigned act = __ballot_sync(0xffffffffu, valid);
+        unsigned peers = 0;
+        if (valid) {
+            peers = __match_any_sync(act, d);
+            const int rank = __popc(peers & ((1u << lane) - 1u));
+            const int pos = offs[(size_t)d * ntiles + tile] + cnt[w][d] + rank;
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) cnt[w][d] += __popc(peers);
+        __syncwarp();
+    }
+}
+
+// Stable sort of (key, index) pairs by key (0 <= key <= max_key); returns
+// in perm the original positions in key order.
+void stable_sort_by_key(const int *keys, long long nnz, int max_key, int *perm, cudaStream_t st) {
+    if (nnz == 0) return;
+    Tmp ka(nnz * sizeof(int), st), kb(nnz * sizeof(int), st), va(nnz * sizeof(int), st),
+        vb(nnz * sizeof(int), st);
+    GB_CUDA(cudaMemcpyAsync(ka.p, keys, nnz * sizeof(int), cudaMemcpyDeviceToDevice, st));
+    launch(k_iota, blocks_for(nnz, 256), 256, st, va.as<int>(), nnz);
+    const int ntiles = ceil_div(nnz, kRsTile);
+    const long long hsz = 256LL * ntiles;
+    Tmp H(hsz * sizeof(int), st), offs((hsz + 1) * sizeof(int), st);
+    int *kin = ka.as<int>(), *kout = kb.as<int>(), *vin = va.as<int>(), *vout = vb.as<int>();
+    int shift = 0;
+    do {
+        const int grid = ceil_div(ntiles, kRsWarps);
+        launch(k_radix_hist, grid, kRsWarps * 32, st, kin, nnz, shift, ntiles, H.as<int>());
+        exclusive_scan(H.as<int>(), (int)hsz, offs.as<int>(), st);
+        launch(k_radix_scatter, grid, kRsWarps * 32, st, kin, vin, nnz, shift, ntiles, offs.as<int>(), kout, vout);
+        GB_CUDA(cudaGetLastError());
+        std::swap(kin, kout);
+        std::swap(vin, vout);
+        shift += 8;
+    } while (shift < 31 && (max_key >> shift) > 0);
+    GB_CUDA(cudaMemcpyAsync(perm, vin, nnz * sizeof(int), cudaMemcpyDeviceToDevice, st));
+}
+
+// --------------------------------------------------------------- transpose
+
+__global__ void k_expand_rows(const int *rp, int nrows, int *rowidx) {
+    const int row = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= nrows) return;
+    for (int k = rp[row] + lane; k < rp[row + 1]; k += 32) rowidx[k] = row;
+}
+
+__global__ void k_count_cols(const int *col, long long nnz, int *cnt) {
+    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nnz) atomicAdd(cnt + col[k], 1);
+}
+
+__global__ void k_gather_t(const int *perm, const int *rowidx, const double *val, long long nnz, int *tcol,
+                           double *tval) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nnz) {
+        const int s = perm[i];
+        tcol[i] = rowidx[s];
+        tval[i] = val[s];
+    }
+}
+
+struct Csr {
+    int nrows = 0, ncols = 0;
+    long long nnz = 0;
+    DevBuf rp, col, val;  // int, int, double
+};
+
+// CSR of M' (sorted rows) from the CSR of M (Section 4.3.3: the CSC of M
+// read as the CSR of M').
+Csr transpose(const int *rp, const int *col, const double *val, int nrows, int ncols, long long nnz,
+              cudaStream_t st) {
+    Csr T;
+    T.nrows = ncols;
+    T.ncols = nrows;
+    T.nnz = nnz;
+    T.rp.alloc((size_t)(ncols + 1) * sizeof(int));
+    T.col.alloc(std::max<long long>(nnz, 1) * sizeof(int));
+    T.val.alloc(std::max<long long>(nnz, 1) * sizeof(double));
+    Tmp cnt((size_t)std::max(ncols, 1) * sizeof(int), st);
+    GB_CUDA(cudaMemsetAsync(cnt.p, 0, (size_t)std::max(ncols, 1) * sizeof(int), st));
+    if (nnz > 0) launch(k_count_cols, blocks_for(nnz, 256), 256, st, col, nnz, cnt.as<int>());
+    exclusive_scan(cnt.as<int>(), ncols, T.rp.as<int>(), st);
+    if (nnz > 0) {
+        Tmp rowidx(nnz * sizeof(int), st), perm(nnz * sizeof(int), st);
+        launch(k_expand_rows, warp_blocks(nrows), kThreads, st, rp, nrows, rowidx.as<int>());
+        stable_sort_by_key(col, nnz, std::max(ncols - 1, 0), perm.as<int>(), st);
+        launch(k_gather_t, blocks_for(nnz, 256), 256, st, perm.as<int>(), rowidx.as<int>(), val, nnz,
+                                                         T.col.as<int>(), T.val.as<double>());
+    }
+    GB_CUDA(cudaGetLastError());
+    return T;
+}
+
+// ----------------------------------------------------------- full P from U
+
+__global__ void k_fullp_len(const int *urp, const int *utrp, const int *utcol, int n, int *len) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int lt = utrp[i + 1] - utrp[i];
+    const int dg = (lt > 0 && utcol[utrp[i + 1] - 1] == i) ? 1 : 0;
+    len[i] = (urp[i + 1] - urp[i]) + lt - dg;
+}
+
+__global__ void k_fullp_fill(const int *urp, const int *ucol, const double *uval, const int *utrp,
+                             const int *utcol, const double *utval, int n, const int *frp, int *fcol,
+                             double *fval) {
+    const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    const int t0 = utrp[i], t1 = utrp[i + 1];
+    const int dg = (t1 > t0 && utcol[t1 - 1] == i) ? 1 : 0;
+    const int nl = t1 - t0 - dg;
+    int out = frp[i];
+    for (int k = lane; k < nl; k += 32) {
+        fcol[out + k] = utcol[t0 + k];
+        fval[out + k] = utval[t0 + k];
+    }
+    out += nl;
+    const int u0 = urp[i], nu = urp[i + 1] - u0;
+    for (int k = lane; k < nu; k += 32) {
+        fcol[out + k] = ucol[u0 + k];
+        fval[out + k] = uval[u0 + k];
+    }
+}
+
+// ------------------------------------------------------------------ Ruiz
+
+__device__ __forceinline__ double limit_scaling(double v) {
+    // norms below 1e-4 are taken as 1, norms above 1e4 as 1e4
+    return v < 1e-4 ? 1.0 : (v > 1e4 ? 1e4 : v);
+}
+
+// out[r] = max(max|M1 row r|, max|M2 row r|) (M2 optional), one warp per row.
+__global__ void k_rownorm(const int *rp1, const double *v1, const int *rp2, const double *v2, int nrows,
+                          double *out) {
+    const int r = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= nrows) return;
+    double mx = 0.0;
+    for (int k = rp1[r] + lane; k < rp1[r + 1]; k += 32) mx = fmax(mx, fabs(v1[k]));
+    if (rp2)
+        for (int k = rp2[r] + lane; k < rp2[r + 1]; k += 32) mx = fmax(mx, fabs(v2[k]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    if (lane == 0) out[r] = mx;
+}
+
+// delta = 1/sqrt(limit(norm)); accumulated scaling *= delta.
+__global__ void k_delta(const double *norm, int n, double *delta, double *acc) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double d = 1.0 / sqrt(limit_scaling(norm[i]));
+    delta[i] = d;
+    acc[i] *= d;
+}
+
+// M <- diag(rs) M diag(cs), one warp per row: v = (v * rs[r]) * cs[c].
+__global__ void k_scale_csr(const int *rp, const int *col, double *val, int nrows, const double *rs,
+                            const double *cs) {
+    const int r = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= nrows) return;
+    const double a = rs[r];
+    for (int k = rp[r] + lane; k < rp[r + 1]; k += 32) val[k] = (val[k] * a) * cs[col[k]];
+}
+
+__global__ void k_scale_vec(double *v, const double *s, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = s[i] * v[i];
+}
+
+// Cost scaling: gamma = 1 / limit(max(mean_j ||P_j||_inf, ||q||_inf)); c *= gamma.
+// scal[0] = c, scal[1] = gamma.  Partial sums per CTA, last CTA finishes.
+__global__ void k_cost_scale(const int *prp, const double *pval, int n, const double *q, double *partials,
+                             unsigned int *ticket, double *scal) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double sum = 0.0, qmax = 0.0;
+    const int nwarps_grid = gridDim.x * kWarps;
+    for (int r = blockIdx.x * kWarps + warp; r < n; r += nwarps_grid) {
+        double mx = 0.0;
+        for (int k = prp[r] + lane; k < prp[r + 1]; k += 32) mx = fmax(mx, fabs(pval[k]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+        if (lane == 0) sum += mx;
+    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        qmax = fmax(qmax, fabs(q[i]));
+    Red<1, 1> red;
+    red.s[0] = sum;
+    red.m[0] = qmax;
+    auto fin = [&](const Red<1, 1> &t) {
+        if (threadIdx.x == 0) {
+            const double mean = n > 0 ? t.s[0] / n : 0.0;
+            const double g = 1.0 / limit_scaling(fmax(mean, t.m[0]));
+            scal[1] = g;
+            scal[0] *= g;
+        }
+    };
+    grid_finish<1, 1>(red, partials, ticket, fin);
+}
+
+__global__ void k_scale_by(double *v, long long n, const double *g) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] *= *g;
+}
+
+__global__ void k_fill(double *v, long long n, double a) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = a;
+}
+
+__global__ void k_scale_bounds(double *l, double *u, const double *E, int m) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    if (isfinite(l[i])) l[i] = E[i] * l[i];
+    if (isfinite(u[i])) u[i] = E[i] * u[i];
+}
+
+// ----------------------------------------------------------- [P A'] build
+
+__global__ void k_pat_rowptr(const int *prp, const int *atrp, int n, int *patrp, int *pend) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > n) return;
+    patrp[i] = prp[i] + atrp[i];
+    if (i < n) pend[i] = prp[i] + atrp[i] + (prp[i + 1] - prp[i]);
+}
+
+__global__ void k_pat_fill(const int *prp, const int *pcol, const double *pval, const int *atrp,
+                           const int *atcol, const double *atval, int n, const int *patrp, int *patcol,
+                           double *patval) {
+    const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    int out = patrp[i];
+    const int p0 = prp[i], np = prp[i + 1] - p0;
+    for (int k = lane; k < np; k += 32) {
+        patcol[out + k] = pcol[p0 + k];
+        patval[out + k] = pval[p0 + k];
+    }
+    out += np;
+    const int a0 = atrp[i], na = atrp[i + 1] - a0;
+    for (int k = lane; k < na; k += 32) {
+        patcol[out + k] = atcol[a0 + k] + n;
+        patval[out + k] = atval[a0 + k];
+    }
+}
+
+// diag(P_bar) and ||A_bar column i||_2^2 (row i of A_bar'), one warp per i.
+__global__ void k_diag_colsq(const int *prp, const int *pcol, const double *pval, const int *atrp,
+                             const double *atval, int n, double *diagP, double *colsq) {
+    const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    double d = 0.0, s = 0.0;
+    for (int k = prp[i] + lane; k < prp[i + 1]; k += 32)
+        if (pcol[k] == i) d = pval[k];
+    for (int k = atrp[i] + lane; k < atrp[i + 1]; k += 32) s += atval[k] * atval[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        d += __shfl_down_sync(0xffffffffu, d, o);
+        s += __shfl_down_sync(0xffffffffu, s, o);
+    }
+    if (lane == 0) {
+        diagP[i] = d;
+        colsq[i] = s;
+    }
+}
+
+__global__ void k_qnorms(const double *q, const double *D, int n, unsigned long long *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double a = fabs(q[i]);
+    atomicMax(out, (unsigned long long)__double_as_longlong(a));
+    atomicMax(out + 1, (unsigned long long)__double_as_longlong(a / D[i]));
+}
+
+// ------------------------------------------------------------ host pieces
+
+struct Input {
+    const int64_t *rp64 = nullptr;
+    const int32_t *col = nullptr;
+    const double *val = nullptr;
+    DevBuf rp64_dev, col_dev, val_dev;  // used when the input is on the host
+};
+
+void stage(const gbosqp_csr &M, bool host, Input &in, cudaStream_t st) {
+    if (!host) {
+        in.rp64 = M.rowptr;
+        in.col = M.colind;
+        in.val = M.val;
+        return;
+    }
+    in.rp64_dev.alloc((size_t)(M.nrows + 1) * sizeof(int64_t));
+    in.col_dev.alloc(std::max<int64_t>(M.nnz, 1) * sizeof(int32_t));
+    in.val_dev.alloc(std::max<int64_t>(M.nnz, 1) * sizeof(double));
+    GB_CUDA(cudaMemcpyAsync(in.rp64_dev.p, M.rowptr, (M.nrows + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    if (M.nnz > 0) {
+        GB_CUDA(cudaMemcpyAsync(in.col_dev.p, M.colind, M.nnz * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        GB_CUDA(cudaMemcpyAsync(in.val_dev.p, M.val, M.nnz * sizeof(double), cudaMemcpyHostToDevice, st));
+    }
+    in.rp64 = in.rp64_dev.as<int64_t>();
+    in.col = in.col_dev.as<int32_t>();
+    in.val = in.val_dev.as<double>();
+}
+
+// Own FP64 copy of a validated input matrix with int32 row pointers.
+Csr own_copy(const gbosqp_csr &M, const Input &in, cudaStream_t st) {
+    Csr C;
+    C.nrows = M.nrows;
+    C.ncols = M.ncols;
+    C.nnz = M.nnz;
+    C.rp.alloc((size_t)(M.nrows + 1) * sizeof(int));
+    C.col.alloc(std::max<int64_t>(M.nnz, 1) * sizeof(int));
+    C.val.alloc(std::max<int64_t>(M.nnz, 1) * sizeof(double));
+    launch(k_rowptr_i32, blocks_for(M.nrows + 1, 256), 256, st, in.rp64, M.nrows + 1, C.rp.as<int>());
+    if (M.nnz > 0) {
+        GB_CUDA(cudaMemcpyAsync(C.col.p, in.col, M.nnz * sizeof(int), cudaMemcpyDeviceToDevice, st));
+        GB_CUDA(cudaMemcpyAsync(C.val.p, in.val, M.nnz * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+    return C;
+}
+
+std::string flag_text(int f) {
+    std::string s;
+    if (f & kFlagRowptr) s += "row pointers not monotone or not [0..nnz]; ";
+    if (f & kFlagColRange) s += "column index out of range; ";
+    if (f & kFlagColOrder) s += "columns not strictly increasing within a row (unsorted or duplicate); ";
+    if (f & kFlagValue) s += "non-finite matrix value; ";
+    if (f & kFlagLower) s += "entry below the diagonal in upper-triangular P; ";
+    if (f & kFlagQ) s += "non-finite q; ";
+    if (f & kFlagBounds) s += "l > u, NaN bound, or l = +inf / u = -inf; ";
+    return s;
+}
+
+int flag_code(int f) {
+    if (f & (kFlagRowptr | kFlagColRange | kFlagColOrder | kFlagLower)) return GBOSQP_ERR_CSR;
+    if (f & kFlagBounds) return GBOSQP_ERR_BOUNDS;
+    return GBOSQP_ERR_NONFINITE;
+}
+
+}  // namespace
+
+SetupData device_setup(const gbosqp_csr &P, const gbosqp_csr &A, const double *q, const double *l,
+                       const double *u, const gbosqp_settings &s, cudaStream_t st) {
+    const int n = P.nrows, m = A.nrows;
+    const bool host = s.input_location == GBOSQP_HOST;
+    SetupData sd;
+    sd.n = n;
+    sd.m = m;
+    sd.nnzA = A.nnz;
+
+    // ---- 1. stage and validate
+    Input inP, inA;
+    stage(P, host, inP, st);
+    stage(A, host, inA, st);
+    DevBuf qv, lv, uv;
+    const double *qd = q, *ld = l, *ud = u;
+    if (host) {
+        qv.alloc((size_t)std::max(n, 1) * sizeof(double));
+        lv.alloc((size_t)std::max(m, 1) * sizeof(double));
+        uv.alloc((size_t)std::max(m, 1) * sizeof(double));
+        if (n) GB_CUDA(cudaMemcpyAsync(qv.p, q, n * sizeof(double), cudaMemcpyHostToDevice, st));
+        if (m) GB_CUDA(cudaMemcpyAsync(lv.p, l, m * sizeof(double), cudaMemcpyHostToDevice, st));
+        if (m) GB_CUDA(cudaMemcpyAsync(uv.p, u, m * sizeof(double), cudaMemcpyHostToDevice, st));
+        qd = qv.as<double>();
+        ld = lv.as<double>();
+        ud = uv.as<double>();
+    }
+    sd.q.alloc((size_t)std::max(n, 1) * sizeof(double));
+    sd.l.alloc((size_t)std::max(m, 1) * sizeof(double));
+    sd.u.alloc((size_t)std::max(m, 1) * sizeof(double));
+    DevBuf flags(sizeof(int));
+    GB_CUDA(cudaMemsetAsync(flags.p, 0, sizeof(int), st));
+    launch(k_check_rowptr, blocks_for(n + 1, 256), 256, st, inP.rp64, n, P.nnz, flags.as<int>());
+    launch(k_check_rowptr, blocks_for(m + 1, 256), 256, st, inA.rp64, m, A.nnz, flags.as<int>());
+    launch(k_check_vectors, blocks_for(std::max(n, m), 256), 256, st, 
+        qd, n, ld, ud, m, sd.q.as<double>(), sd.l.as<double>(), sd.u.as<double>(), flags.as<int>());
+    GB_CUDA(cudaGetLastError());
+    int hflags = 0;
+    GB_CUDA(cudaMemcpyAsync(&hflags, flags.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GB_CUDA(cudaStreamSynchronize(st));
+    if (hflags & kFlagRowptr) fail(GBOSQP_ERR_CSR, "invalid CSR: " + flag_text(hflags));
+    Csr Pin = own_copy(P, inP, st);
+    Csr Ain = own_copy(A, inA, st);
+    launch(k_check_rows, warp_blocks(n), kThreads, st, Pin.rp.as<int>(), Pin.col.as<int>(), Pin.val.as<double>(), n,
+                                                      n, s.P_is_upper ? 1 : 0, flags.as<int>());
+    launch(k_check_rows, warp_blocks(m), kThreads, st, Ain.rp.as<int>(), Ain.col.as<int>(), Ain.val.as<double>(), m,
+                                                      A.ncols, 0, flags.as<int>());
+    GB_CUDA(cudaGetLastError());
+    GB_CUDA(cudaMemcpyAsync(&hflags, flags.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    GB_CUDA(cudaStreamSynchronize(st));
+    if (hflags) fail(flag_code(hflags), "invalid problem data: " + flag_text(hflags));
+    inP = Input();
+    inA = Input();
+    qv.release();
+    lv.release();
+    uv.release();
+
+    // ---- 2. full P and A'
+    Csr Pf;
+    if (s.P_is_upper) {
+        Csr Ut = transpose(Pin.rp.as<int>(), Pin.col.as<int>(), Pin.val.as<double>(), n, n, Pin.nnz, st);
+        Tmp len((size_t)std::max(n, 1) * sizeof(int), st);
+        launch(k_fullp_len, blocks_for(n, 256), 256, st, Pin.rp.as<int>(), Ut.rp.as<int>(), Ut.col.as<int>(), n,
+                                                         len.as<int>());
+        Pf.nrows = Pf.ncols = n;
+        Pf.rp.alloc((size_t)(n + 1) * sizeof(int));
+        exclusive_scan(len.as<int>(), n, Pf.rp.as<int>(), st);
+        int total = 0;
+        GB_CUDA(cudaMemcpyAsync(&total, Pf.rp.as<int>() + n, sizeof(int), cudaMemcpyDeviceToHost, st));
+        GB_CUDA(cudaStreamSynchronize(st));
+        Pf.nnz = total;
+        Pf.col.alloc(std::max(total, 1) * sizeof(int));
+        Pf.val.alloc(std::max(total, 1) * sizeof(double));
+        launch(k_fullp_fill, warp_blocks(n), kThreads, st, Pin.rp.as<int>(), Pin.col.as<int>(), Pin.val.as<double>(),
+                                                          Ut.rp.as<int>(), Ut.col.as<int>(), Ut.val.as<double>(), n,
+                                                          Pf.rp.as<int>(), Pf.col.as<int>(), Pf.val.as<double>());
+        GB_CUDA(cudaGetLastError());
+        GB_CUDA(cudaStreamSynchronize(st));
+    } else {
+        Pf = std::move(Pin);
+    }
+    Pin = Csr();
+    Csr At = transpose(Ain.rp.as<int>(), Ain.col.as<int>(), Ain.val.as<double>(), m, n, Ain.nnz, st);
+    sd.nnzP = Pf.nnz;
+
+    // ---- 3. Ruiz equilibration (Algorithm 2)
+    sd.D.alloc((size_t)std::max(n, 1) * sizeof(double));
+    sd.E.alloc((size_t)std::max(m, 1) * sizeof(double));
+    Tmp nx((size_t)std::max(n, 1) * sizeof(double), st), nz((size_t)std::max(m, 1) * sizeof(double), st);
+    Tmp dx((size_t)std::max(n, 1) * sizeof(double), st), dz((size_t)std::max(m, 1) * sizeof(double), st);
+    Tmp scal(2 * sizeof(double), st);
+    const int cs_grid = std::max(1, std::min(ceil_div(std::max(n, 1), kWarps), device_sm_count() * 4));
+    Tmp partials((size_t)cs_grid * 2 * sizeof(double), st), ticket(sizeof(unsigned int), st);
+    GB_CUDA(cudaMemsetAsync(ticket.p, 0, sizeof(unsigned int), st));
+    launch(k_fill, blocks_for(n, 256), 256, st, sd.D.as<double>(), n, 1.0);
+    launch(k_fill, blocks_for(m, 256), 256, st, sd.E.as<double>(), m, 1.0);
+    launch(k_fill, 1, 32, st, scal.as<double>(), 1, 1.0);
+    for (int pass = 0; pass < s.scaling_iters; ++pass) {
+        // column inf-norms of [[P, A'], [A, 0]]: columns j <= n are rows of
+        // P and A'; columns n + i are rows of A
+        if (n) launch(k_rownorm, warp_blocks(n), kThreads, st, Pf.rp.as<int>(), Pf.val.as<double>(), At.rp.as<int>(),
+                                                             At.val.as<double>(), n, nx.as<double>());
+        if (m) launch(k_rownorm, warp_blocks(m), kThreads, st, Ain.rp.as<int>(), Ain.val.as<double>(), nullptr, nullptr,
+                                                             m, nz.as<double>());
+        if (n) launch(k_delta, blocks_for(n, 256), 256, st, nx.as<double>(), n, dx.as<double>(), sd.D.as<double>());
+        if (m) launch(k_delta, blocks_for(m, 256), 256, st, nz.as<double>(), m, dz.as<double>(), sd.E.as<double>());
+        // P <- dx P dx, A <- dz A dx, A' <- dx A' dz, q <- dx q
+        if (n) launch(k_scale_csr, warp_blocks(n), kThreads, st, Pf.rp.as<int>(), Pf.col.as<int>(), Pf.val.as<double>(),
+                                                               n, dx.as<double>(), dx.as<double>());
+        if (m) launch(k_scale_csr, warp_blocks(m), kThreads, st, Ain.rp.as<int>(), Ain.col.as<int>(),
+                                                               Ain.val.as<double>(), m, dz.as<double>(), dx.as<double>());
+        if (n) launch(k_scale_csr, warp_blocks(n), kThreads, st, At.rp.as<int>(), At.col.as<int>(), At.val.as<double>(),
+                                                               n, dx.as<double>(), dz.as<double>());
+        if (n) launch(k_scale_vec, blocks_for(n, 256), 256, st, sd.q.as<double>(), dx.as<double>(), n);
+        // cost scaling
+        launch(k_cost_scale, cs_grid, kThreads, st, Pf.rp.as<int>(), Pf.val.as<double>(), n, sd.q.as<double>(),
+                                                   partials.as<double>(), ticket.as<unsigned int>(), scal.as<double>());
+        if (Pf.nnz) launch(k_scale_by, blocks_for(Pf.nnz, 256), 256, st, Pf.val.as<double>(), Pf.nnz, scal.as<double>() + 1);
+        if (n) launch(k_scale_by, blocks_for(n, 256), 256, st, sd.q.as<double>(), n, scal.as<double>() + 1);
+        GB_CUDA(cudaGetLastError());
+    }
+    if (m) launch(k_scale_bounds, blocks_for(m, 256), 256, st, sd.l.as<double>(), sd.u.as<double>(), sd.E.as<double>(), m);
+    GB_CUDA(cudaMemcpyAsync(&sd.c, scal.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+
+    // ---- 4. [P A'], Jacobi data, q norms
+    sd.nnzPAt = Pf.nnz + At.nnz;
+    if (sd.nnzPAt >= (1LL << 31) || A.nnz >= (1LL << 31))
+        fail(GBOSQP_ERR_UNSUPPORTED, "more than 2^31-1 nonzeros in A or [P A']");
+    sd.PAt_rowptr.alloc((size_t)(n + 1) * sizeof(int));
+    sd.PAt_pend.alloc((size_t)std::max(n, 1) * sizeof(int));
+    sd.PAt_col.alloc(std::max<long long>(sd.nnzPAt, 1) * sizeof(int));
+    sd.PAt_val.alloc(std::max<long long>(sd.nnzPAt, 1) * sizeof(double));
+    launch(k_pat_rowptr, blocks_for(n + 1, 256), 256, st, Pf.rp.as<int>(), At.rp.as<int>(), n,
+                                                          sd.PAt_rowptr.as<int>(), sd.PAt_pend.as<int>());
+    if (n) launch(k_pat_fill, warp_blocks(n), kThreads, st, Pf.rp.as<int>(), Pf.col.as<int>(), Pf.val.as<double>(),
+                                                          At.rp.as<int>(), At.col.as<int>(), At.val.as<double>(), n,
+                                                          sd.PAt_rowptr.as<int>(), sd.PAt_col.as<int>(),
+                                                          sd.PAt_val.as<double>());
+    sd.diagP.alloc((size_t)std::max(n, 1) * sizeof(double));
+    sd.colsq.alloc((size_t)std::max(n, 1) * sizeof(double));
+    if (n) launch(k_diag_colsq, warp_blocks(n), kThreads, st, Pf.rp.as<int>(), Pf.col.as<int>(), Pf.val.as<double>(),
+                                                            At.rp.as<int>(), At.val.as<double>(), n,
+                                                            sd.diagP.as<double>(), sd.colsq.as<double>());
+    Tmp qn(2 * sizeof(unsigned long long), st);
+    GB_CUDA(cudaMemsetAsync(qn.p, 0, 2 * sizeof(unsigned long long), st));
+    if (n) launch(k_qnorms, blocks_for(n, 256), 256, st, sd.q.as<double>(), sd.D.as<double>(), n,
+                                                        qn.as<unsigned long long>());
+    double qnh[2] = {0.0, 0.0};
+    GB_CUDA(cudaMemcpyAsync(qnh, qn.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    GB_CUDA(cudaGetLastError());
+    // A keeps its own copy; host row pointers for the work plans
+    sd.A_rowptr = std::move(Ain.rp);
+    sd.A_col = std::move(Ain.col);
+    sd.A_val = std::move(Ain.val);
+    sd.A_rowptr_host.resize(m + 1);
+    sd.PAt_rowptr_host.resize(n + 1);
+    GB_CUDA(cudaMemcpyAsync(sd.A_rowptr_host.data(), sd.A_rowptr.p, (m + 1) * sizeof(int), cudaMemcpyDeviceToHost, st));
+    GB_CUDA(cudaMemcpyAsync(sd.PAt_rowptr_host.data(), sd.PAt_rowptr.p, (n + 1) * sizeof(int),
+                            cudaMemcpyDeviceToHost, st));
+    GB_CUDA(cudaStreamSynchronize(st));
+    sd.qnorm_s = qnh[0];
+    sd.qnorm_u = qnh[1];
+    return sd;
+}
+
+}  // namespace gb

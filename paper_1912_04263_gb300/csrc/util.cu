@@ -1,0 +1,89 @@
+// Host utilities: errors, device buffers, launch geometry, and the
+// row-block work plan of the CSR SpMV kernels.
+#include <algorithm>
+#include <string>
+
+#include "common.cuh"
+
+namespace gb {
+
+thread_local long long g_launches = 0;
+
+void fail(int code, const std::string &msg) { throw GbError{code, msg}; }
+
+void check_cuda(cudaError_t e, const char *what, const char *file, int line) {
+    if (e == cudaSuccess) return;
+    cudaGetLastError();
+    const int code = (e == cudaErrorMemoryAllocation) ? GBOSQP_ERR_OOM : GBOSQP_ERR_CUDA;
+    throw GbError{code, std::string(what) + ": " + cudaGetErrorString(e) + " (" + file + ":" + std::to_string(line) + ")"};
+}
+
+void DevBuf::alloc(size_t nbytes) {
+    release();
+    if (nbytes == 0) nbytes = 16;
+    cudaError_t e = cudaMalloc(&p, nbytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+        fail(GBOSQP_ERR_OOM, "cudaMalloc of " + std::to_string(nbytes) + " bytes failed: " + cudaGetErrorString(e));
+    }
+    bytes = nbytes;
+}
+
+void DevBuf::release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+}
+
+int device_sm_count() {
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return std::max(sms, 1);
+}
+
+int grid_for_items(int nitems, const void *kernel, int smem_dynamic) {
+    int per_sm = 0;
+    GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem_dynamic));
+    per_sm = std::max(per_sm, 1);
+    return std::max(1, std::min(nitems, device_sm_count() * per_sm));
+}
+
+int grid_for_n(long long n, int threads) { return (int)std::max(1LL, (n + threads - 1) / threads); }
+
+// Cut the rows into work items: runs of consecutive rows with at most kCap
+// nonzeros and at most kCap rows; a row longer than kCap becomes ceil(len /
+// kCap) pieces of nearly equal length, combined by the last piece.
+HostPlan build_plan(const std::vector<int> &rp) {
+    HostPlan hp;
+    const int nrows = (int)rp.size() - 1;
+    int r = 0;
+    while (r < nrows) {
+        const long long len = (long long)rp[r + 1] - rp[r];
+        if (len > kCap) {
+            const int np = (int)((len + kCap - 1) / kCap);
+            const int id = (int)hp.longrows.size();
+            hp.longrows.push_back(LongRow{(int)hp.items.size(), np});
+            for (int p = 0; p < np; ++p) {
+                const int k0 = rp[r] + (int)(len * p / np);
+                const int k1 = rp[r] + (int)(len * (p + 1) / np);
+                hp.items.push_back(Item{r, -(id + 1), k0, k1});
+            }
+            ++r;
+            continue;
+        }
+        const int r0 = r;
+        long long tot = 0;
+        while (r < nrows) {
+            const long long l = (long long)rp[r + 1] - rp[r];
+            if (l > kCap || tot + l > kCap || r - r0 >= kCap) break;
+            tot += l;
+            ++r;
+        }
+        hp.items.push_back(Item{r0, r, rp[r0], rp[r]});
+    }
+    return hp;
+}
+
+}  // namespace gb

@@ -13,6 +13,7 @@ from .problems import (  # noqa: F401
     equality_qp,
     box_qp,
     tiny_qp,
+    rowlen_qp,
     infeasible_primal_qp,
     infeasible_dual_qp,
     by_name,

@@ -189,6 +189,42 @@ def tiny_qp(n: int, m: int, seed: int, n_eq: int = 0, n_inf: int = 0) -> QP:
               name=f"tiny_n{n}_m{m}_s{seed}", meta=dict(kind="tiny", seed=seed))
 
 
+def rowlen_qp(row_lengths, n: int, seed: int, zero_p_every: int = 3) -> QP:
+    """A with prescribed row lengths (distinct uniform columns, N(0,1)
+    values) and a diagonal P that is zero on every zero_p_every-th entry
+    (empty rows of P).  For exercising SpMV work splitting: empty rows, rows
+    at and around the per-item capacity, and very long rows."""
+    rows, cols = [], []
+    st = Stream(seed, "rowlen/cols")
+    for i, L in enumerate(row_lengths):
+        L = int(min(L, n))
+        if L:
+            # distinct uniform columns: first occurrences of uniform draws
+            k = 2 * L + 16
+            while True:
+                idx = np.floor(st.uniform(k) * n).astype(np.int64)
+                _, first = np.unique(idx, return_index=True)
+                if first.size >= L:
+                    break
+                k *= 2
+            c = np.sort(idx[np.sort(first)[:L]])
+            rows.append(np.full(L, i, np.int64))
+            cols.append(c.astype(np.int64))
+    rows = np.concatenate(rows) if rows else np.zeros(0, np.int64)
+    cols = np.concatenate(cols) if cols else np.zeros(0, np.int64)
+    vals = Stream(seed, "rowlen/vals").normal(rows.size)
+    m = len(row_lengths)
+    A = _csr(rows, cols, vals, (m, n))
+    pd = 0.5 + Stream(seed, "rowlen/pd").uniform(n)
+    if zero_p_every:
+        pd[::zero_p_every] = 0.0
+    P = _clean(sp.diags(pd))
+    q = Stream(seed, "rowlen/q").normal(n)
+    l = -Stream(seed, "rowlen/l").uniform(m) - 0.1
+    u = Stream(seed, "rowlen/u").uniform(m) + 0.1
+    return QP(P, q, A, l, u, name=f"rowlen_m{m}_n{n}_s{seed}", meta=dict(kind="rowlen", seed=seed))
+
+
 def infeasible_primal_qp() -> QP:
     """x1 >= 1 and x1 <= 0 (plus a harmless second variable)."""
     P = _clean(sp.identity(2))

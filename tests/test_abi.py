@@ -1,0 +1,89 @@
+"""The C-ABI library loads and exports every entry point declared in
+include/gbosqp.h; host-only calls behave (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import qpgen
+from oracle import checks, admm
+from tests.conftest import ROOT
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1912_04263_gb300 import binding
+    return binding.lib()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "gbosqp.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?(?:int|void|char)\s*\*?\s*(\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_core_calls():
+    names = declared_functions()
+    for core in ["osqp_setup", "osqp_solve", "osqp_update_rho", "osqp_get_solution", "osqp_get_info",
+                 "osqp_cleanup", "gbosqp_default_settings", "gbosqp_last_error"]:
+        assert core in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_default_settings_match_the_paper(lib):
+    from paper_1912_04263_gb300 import binding as gb
+    s = gb.default_settings()
+    # Section 3.4 defaults, Table 1 cadence, Section 5.3.4 tolerance rule
+    assert s.alpha == 1.6 and s.sigma == 1e-6
+    assert s.check_every == 5 and s.rho_every == 10
+    assert s.pcg_lambda == 0.15 and s.pcg_eps_min == 1e-7
+    assert s.rho0 == 0.1 and s.eps_abs == 1e-3 and s.eps_rel == 1e-3
+
+
+def test_error_strings_and_null_arguments(lib):
+    from paper_1912_04263_gb300 import binding as gb
+    assert gb.error_string(gb.SOLVED) == "solved"
+    assert gb.error_string(gb.ERR_CSR) == "invalid CSR matrix"
+    assert lib.osqp_solve(None) == gb.ERR_INVALID_ARG
+    assert lib.gbosqp_default_settings(None) == gb.ERR_INVALID_ARG
+    lib.osqp_cleanup(None)
+    h = ctypes.c_void_p()
+    assert lib.osqp_setup(ctypes.byref(h), None, None, None, None, None, None) == gb.ERR_INVALID_ARG
+
+
+def test_settings_validation_is_host_side(lib):
+    from paper_1912_04263_gb300 import binding as gb
+    qp = qpgen.random_qp(5, 7, 0)
+    for bad in [dict(alpha=2.0), dict(sigma=0.0), dict(check_every=0), dict(rho_every=7),
+                dict(precision=5), dict(rho_policy=gb.RHO_LEARNED)]:
+        with pytest.raises(gb.GbosqpError) as e:
+            gb.Solver(qp, **bad)
+        assert e.value.code == gb.ERR_INVALID_ARG, bad
+
+
+def test_objective_error_bound_holds_on_loose_iterates():
+    """The bound used by the GPU parity tests holds for oracle iterates at a
+    loose tolerance (exact optimum from brute force)."""
+    checked = 0
+    for seed in range(8):
+        qp = qpgen.tiny_qp(4, 6, seed, n_eq=1, n_inf=1)
+        try:
+            xs, ys = checks.brute_force(qp)
+        except RuntimeError:  # an infeasible draw
+            continue
+        checked += 1
+        fs = admm.objective(qp.P, qp.q, xs)
+        r = admm.solve(qp, admm.Settings(eps_abs=1e-2, eps_rel=1e-2, check_every=1))
+        v = checks.kkt_violation(qp, r.x, r.z, r.y)
+        bound = checks.objective_error_bound(r.x, r.y, v.prim, v.dual, xs, ys)
+        assert abs(r.obj - fs) <= bound * (1 + 1e-9) + 1e-12
+    assert checked >= 3
