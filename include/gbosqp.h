@@ -268,10 +268,12 @@ int gbosqp_check(gbosqp_handle *h, double out[GBOSQP_CHECK_FIELDS]);
 #define GBOSQP_K_CHECK_A 5        /* ||Ax - z|| etc., FP64 accumulation (SpMV A)        */
 #define GBOSQP_K_CHECK_B 6        /* ||Px + q + A'y|| etc., FP64 (SpMV [P A'])          */
 
-/* Time `reps` back-to-back launches of one solve kernel on the handle's
- * stream with CUDA events, in the launch configuration the solve uses, on
- * the handle's current vectors (a private copy of the scalar state is used,
- * so the next solve is unaffected).  Writes the mean duration in ms. */
+/* Time `reps` back-to-back launches of one solve kernel, in the launch
+ * configuration the solve uses, on the handle's current vectors: the
+ * launches are captured into one CUDA graph on the handle's stream and the
+ * graph launch is timed with CUDA events (so host launch cost is excluded).
+ * A private copy of the scalar state is used and the iterates are restored,
+ * so the next solve is unaffected.  Writes the mean duration in ms. */
 int gbosqp_bench_kernel(gbosqp_handle *h, int kernel, int32_t reps, double *avg_ms);
 
 #ifdef __cplusplus

@@ -64,7 +64,10 @@ struct DevBuf {
 
 constexpr int kThreads = 256;             // CTA size of every row-block kernel
 constexpr int kWarps = kThreads / 32;
-constexpr int kCap = 2048;                // max nonzeros per work item
+#ifndef GB_CAP
+#define GB_CAP 2048
+#endif
+constexpr int kCap = GB_CAP;              // max nonzeros per work item
 constexpr int kPerThread = kCap / kThreads;
 constexpr double kInf = 1e20;             // |bound| >= kInf is infinite
 
@@ -103,6 +106,7 @@ struct CsrDev {
     const LongRow *longrows = nullptr;
     int *lr_count = nullptr;     // one ticket counter per long row (zeroed)
     double *lr_part = nullptr;   // 2 partial sums per item
+    int *err = nullptr;          // set to 1 if a bulk copy wait timed out
 };
 
 // ------------------------------------------------------------ status block
@@ -127,7 +131,7 @@ struct Status {
     // learned policy
     int fallbacks, stall_count, stall_left, policy_disabled;
     double last_merit, prev_merit;
-    int cg_since_update, pad0;
+    int cg_since_update, device_error;
     // last-block tickets, one per kernel kind
     unsigned int tickets[16];
 };
@@ -275,31 +279,61 @@ __device__ __forceinline__ void reduce_rows(const CsrDev<T> &M, const Item &it, 
     }
 }
 
-// Process every item assigned to this CTA (items blockIdx.x, +gridDim.x, ...).
-// gather(c) returns the vector entry for column c in the accumulation type.
+// Dynamic shared memory of a row-block kernel (the products of one item).
+template <class T, class Acc>
+constexpr size_t rowblock_smem() {
+    return (size_t)kCap * sizeof(Acc);
+}
+
+// Load the value/column range of an item into registers (streaming loads:
+// evict-first, so that L1 keeps the gathered vector).
+template <class T>
+__device__ __forceinline__ void load_item(const CsrDev<T> &M, const Item &it, T (&v)[kPerThread], int (&c)[kPerThread]) {
+    const int nnz = it.k1 - it.k0;
+#pragma unroll
+    for (int u = 0; u < kPerThread; ++u) {
+        const int e = u * kThreads + threadIdx.x;
+        if (e < nnz) {
+            v[u] = __ldcs(M.val + it.k0 + e);
+            c[u] = __ldcs(M.col + it.k0 + e);
+        }
+    }
+}
+
+// Process the contiguous range of items assigned to this CTA.  Each step
+// prefetches the next item's values and columns into registers, then
+// multiplies the current item by the gathered vector (into shared memory)
+// and reduces its rows with lane groups sized to the mean row length.
+// Consecutive pieces of a long row accumulate per thread and are reduced
+// once; a long row that crosses a CTA boundary is combined by the last of
+// its contributors, in CTA order.  gather(c) returns the vector entry for
+// column c in the accumulation type; epi.row(r, s1, s2, red) consumes rows.
 template <class Acc, bool SPLIT, class T, class Gather, class Epi, class RedT>
-__device__ __forceinline__ void run_items(const CsrDev<T> &M, const Gather &gather, Epi &epi, RedT &red) {
-    __shared__ Acc sprod[kCap];
-    __shared__ bool last_piece;
+__device__ __forceinline__ bool run_items(const CsrDev<T> &M, const Gather &gather, Epi &epi, RedT &red) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Acc *sprod = reinterpret_cast<Acc *>(smem_raw);
     __shared__ Acc wsum[2][kWarps];
-    for (int itx = blockIdx.x; itx < M.nitems; itx += gridDim.x) {
+    const int Q = (M.nitems + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int i0 = (int)blockIdx.x * Q;
+    const int i1 = min(M.nitems, i0 + Q);
+    T va[kPerThread], vb[kPerThread];
+    int ca[kPerThread], cb[kPerThread];
+    if (i0 < i1) load_item(M, M.items[i0], va, ca);
+    Acc ps1 = Acc(0), ps2 = Acc(0);  // running sums of a long row's pieces
+    for (int itx = i0; itx < i1; ++itx) {
         const Item it = M.items[itx];
+        const bool has_next = itx + 1 < i1;
+        Item nx;
+        if (has_next) {
+            nx = M.items[itx + 1];
+            load_item(M, nx, vb, cb);
+        }
         const int nnz = it.k1 - it.k0;
         if (it.r1 >= 0) {
-            T v[kPerThread];
-            int c[kPerThread];
 #pragma unroll
             for (int u = 0; u < kPerThread; ++u) {
                 const int e = u * kThreads + threadIdx.x;
-                if (e < nnz) {
-                    v[u] = __ldg(M.val + it.k0 + e);
-                    c[u] = __ldg(M.col + it.k0 + e);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < kPerThread; ++u) {
-                const int e = u * kThreads + threadIdx.x;
-                if (e < nnz) sprod[e] = Acc(v[u]) * gather(c[u]);
+                if (e < nnz) sprod[e] = Acc(va[u]) * gather(ca[u]);
             }
             __syncthreads();
             const int R = it.r1 - it.r0;
@@ -311,62 +345,69 @@ __device__ __forceinline__ void run_items(const CsrDev<T> &M, const Gather &gath
             else reduce_rows<1, SPLIT, Acc>(M, it, sprod, epi, red);
             __syncthreads();
         } else {
-            // piece of a long row
             const int row = it.r0;
-            const int lr = -(it.r1 + 1);
-            const int sp = SPLIT ? __ldg(M.pend + row) : 0x7fffffff;
-            Acc s1 = Acc(0), s2 = Acc(0);
-            for (int base = it.k0; base < it.k1; base += kCap) {
-                T v[kPerThread];
-                int c[kPerThread];
+            const int sp = SPLIT ? __ldg(M.pend + row) - it.k0 : 0x7fffffff;
 #pragma unroll
-                for (int u = 0; u < kPerThread; ++u) {
-                    const int k = base + u * kThreads + threadIdx.x;
-                    if (k < it.k1) {
-                        v[u] = __ldg(M.val + k);
-                        c[u] = __ldg(M.col + k);
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < kPerThread; ++u) {
-                    const int k = base + u * kThreads + threadIdx.x;
-                    if (k < it.k1) {
-                        const Acc pr = Acc(v[u]) * gather(c[u]);
-                        if (!SPLIT || k < sp) s1 += pr; else s2 += pr;
-                    }
+            for (int u = 0; u < kPerThread; ++u) {
+                const int e = u * kThreads + threadIdx.x;
+                if (e < nnz) {
+                    const Acc pr = Acc(va[u]) * gather(ca[u]);
+                    if (!SPLIT || e < sp) ps1 += pr; else ps2 += pr;
                 }
             }
+            const bool row_end = !has_next || nx.r1 != it.r1;
+            if (row_end) {
+                Acc s1 = ps1, s2 = ps2;
+                ps1 = Acc(0);
+                ps2 = Acc(0);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                s1 += __shfl_down_sync(0xffffffffu, s1, o);
-                s2 += __shfl_down_sync(0xffffffffu, s2, o);
-            }
-            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-            if (lane == 0) { wsum[0][warp] = s1; wsum[1][warp] = s2; }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                double a1 = 0.0, a2 = 0.0;
-                for (int w = 0; w < kWarps; ++w) { a1 += (double)wsum[0][w]; a2 += (double)wsum[1][w]; }
-                M.lr_part[2 * (size_t)itx] = a1;
-                M.lr_part[2 * (size_t)itx + 1] = a2;
-                __threadfence();
-                const LongRow L = M.longrows[lr];
-                const int t = atomicAdd(M.lr_count + lr, 1);
-                last_piece = (t == L.npieces - 1);
-                if (last_piece) {
-                    __threadfence();
-                    double t1 = 0.0, t2 = 0.0;
-                    for (int p = 0; p < L.npieces; ++p) {
-                        t1 += __ldcg(M.lr_part + 2 * (size_t)(L.first_item + p));
-                        t2 += __ldcg(M.lr_part + 2 * (size_t)(L.first_item + p) + 1);
-                    }
-                    M.lr_count[lr] = 0;
-                    epi.row(row, Acc(t1), Acc(t2), red);
+                for (int o = 16; o > 0; o >>= 1) {
+                    s1 += __shfl_down_sync(0xffffffffu, s1, o);
+                    s2 += __shfl_down_sync(0xffffffffu, s2, o);
                 }
+                const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+                if (lane == 0) { wsum[0][warp] = s1; wsum[1][warp] = s2; }
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    double a1 = 0.0, a2 = 0.0;
+                    for (int w = 0; w < kWarps; ++w) { a1 += (double)wsum[0][w]; a2 += (double)wsum[1][w]; }
+                    const int lr = -(it.r1 + 1);
+                    const LongRow L = M.longrows[lr];
+                    const int first = L.first_item, last = L.first_item + L.npieces - 1;
+                    const int c0 = first / Q, c1 = last / Q;  // CTA ranges covering the row
+                    if (c0 == c1) {
+                        epi.row(row, Acc(a1), Acc(a2), red);
+                    } else {
+                        const int slot = max(first, i0);  // this CTA's first piece of the row
+                        M.lr_part[2 * (size_t)slot] = a1;
+                        M.lr_part[2 * (size_t)slot + 1] = a2;
+                        __threadfence();
+                        const int t = atomicAdd(M.lr_count + lr, 1);
+                        if (t == c1 - c0) {
+                            __threadfence();
+                            double t1 = 0.0, t2 = 0.0;
+                            for (int cc = c0; cc <= c1; ++cc) {
+                                const int sl = max(first, cc * Q);
+                                t1 += __ldcg(M.lr_part + 2 * (size_t)sl);
+                                t2 += __ldcg(M.lr_part + 2 * (size_t)sl + 1);
+                            }
+                            M.lr_count[lr] = 0;
+                            epi.row(row, Acc(t1), Acc(t2), red);
+                        }
+                    }
+                }
+                __syncthreads();
             }
-            __syncthreads();
+        }
+        if (has_next) {
+#pragma unroll
+            for (int u = 0; u < kPerThread; ++u) {
+                va[u] = vb[u];
+                ca[u] = cb[u];
+            }
         }
     }
+    return true;
 }
 
 // ------------------------------------------------------------- utilities
@@ -376,9 +417,10 @@ __device__ __forceinline__ void run_items(const CsrDev<T> &M, const Gather &gath
 // iteration counters instead).
 extern thread_local long long g_launches;
 
-// Launch kern<<<grid, block, 0, stream>>>(args...) and count it.
+// Launch kern<<<grid, block, smem, stream>>>(args...) and count it.
 template <class... KArgs, class... Args>
-inline void launch(void (*kern)(KArgs...), int grid, int block, cudaStream_t stream, Args &&...args) {
+inline void launch_smem(void (*kern)(KArgs...), int grid, int block, size_t smem, cudaStream_t stream,
+                        Args &&...args) {
     std::tuple<KArgs...> vals(std::forward<Args>(args)...);
     void *ptrs[sizeof...(KArgs) > 0 ? sizeof...(KArgs) : 1];
     std::apply([&](auto &...e) {
@@ -386,7 +428,12 @@ inline void launch(void (*kern)(KArgs...), int grid, int block, cudaStream_t str
         ((ptrs[i++] = (void *)&e), ...);
     }, vals);
     ++g_launches;
-    GB_CUDA(cudaLaunchKernel((const void *)kern, dim3(grid > 0 ? grid : 1), dim3(block), ptrs, 0, stream));
+    GB_CUDA(cudaLaunchKernel((const void *)kern, dim3(grid > 0 ? grid : 1), dim3(block), ptrs, smem, stream));
+}
+
+template <class... KArgs, class... Args>
+inline void launch(void (*kern)(KArgs...), int grid, int block, cudaStream_t stream, Args &&...args) {
+    launch_smem(kern, grid, block, 0, stream, std::forward<Args>(args)...);
 }
 
 __host__ __device__ __forceinline__ int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }

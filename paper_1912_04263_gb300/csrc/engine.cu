@@ -149,7 +149,7 @@ struct EpiInit {
 };
 
 template <class T>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_pcg_init(CsrDev<T> PAt, Vecs<T> v, Status *st, double *partials,
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : 2) k_pcg_init(CsrDev<T> PAt, Vecs<T> v, Status *st, double *partials,
                                                        cudaGraphConditionalHandle hP, int use_h) {
     EpiInit<T> epi{v, T(st->sigma)};
     Red<1, 1> red;
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_pcg_init(CsrDev<T> PAt
         st->beta = 0.0;
         st->cg_it = 0;
         st->breakdown = 0;
-        const int cont = (isfinite(t.m[0]) && t.m[0] > st->eps_pcg && st->max_cg > 0) ? 1 : 0;
+        const int cont = (!st->device_error && isfinite(t.m[0]) && t.m[0] > st->eps_pcg && st->max_cg > 0) ? 1 : 0;
         st->pcg_continue = cont;
         if (use_h) cudaGraphSetConditional(hP, cont);
     };
@@ -178,7 +178,7 @@ struct EpiDir {
 };
 
 template <class T>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_pcg_p_t(CsrDev<T> A, Vecs<T> v, const Status *st) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : 2) k_pcg_p_t(CsrDev<T> A, Vecs<T> v, const Status *st) {
     const T beta = T(st->beta);
     const int n = v.n;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
@@ -202,7 +202,7 @@ struct EpiKp {
 };
 
 template <class T>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_pcg_kp(CsrDev<T> PAt, Vecs<T> v, Status *st, double *partials) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : 2) k_pcg_kp(CsrDev<T> PAt, Vecs<T> v, Status *st, double *partials) {
     EpiKp<T> epi{v, T(st->sigma)};
     Red<1, 0> red;
     red.zero();
@@ -249,7 +249,8 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(Vecs<T> v, Status *st, 
         st->rnorm = t.m[0];
         st->cg_it += 1;
         st->cg_total += 1;
-        const int cont = (!st->breakdown && isfinite(t.m[0]) && t.m[0] > st->eps_pcg && st->cg_it < st->max_cg) ? 1 : 0;
+        const int cont = (!st->device_error && !st->breakdown && isfinite(t.m[0]) && t.m[0] > st->eps_pcg &&
+                          st->cg_it < st->max_cg) ? 1 : 0;
         st->pcg_continue = cont;
         if (use_h) cudaGraphSetConditional(hP, cont);
     };
@@ -277,7 +278,7 @@ struct EpiAdmm {
 };
 
 template <class T>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_admm_update(CsrDev<T> A, Vecs<T> v, Status *st) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : 2) k_admm_update(CsrDev<T> A, Vecs<T> v, Status *st) {
     const T alpha = T(st->alpha);
     const T rho = T(st->rho);
     const int n = v.n;
@@ -367,7 +368,7 @@ __global__ void __launch_bounds__(kThreads) k_check_b(CsrDev<T> PAt, Vecs<T> v, 
             const bool finite = isfinite(st->r_prim) && isfinite(st->r_dual) && isfinite(st->rp_s) && isfinite(st->rd_s);
             const bool conv = finite && st->r_prim <= st->eps_prim && st->r_dual <= st->eps_dual;
             int status = 0;
-            if (!finite) status = GBOSQP_NONFINITE;
+            if (!finite || st->device_error) status = GBOSQP_NONFINITE;
             else if (conv) status = GBOSQP_SOLVED;
             else if (st->k >= st->max_iter) status = GBOSQP_MAX_ITER;
             st->status = status;
@@ -509,8 +510,8 @@ __global__ void k_proj_z(Vecs<T> v) {
 // ----------------------------------------------------- graph construction
 
 template <class... KArgs, class... Args>
-cudaGraphNode_t add_kernel(cudaGraph_t g, const cudaGraphNode_t *dep, void (*kern)(KArgs...), int grid,
-                           Args &&...args) {
+cudaGraphNode_t add_kernel_smem(cudaGraph_t g, const cudaGraphNode_t *dep, void (*kern)(KArgs...), int grid,
+                                size_t smem, Args &&...args) {
     std::tuple<KArgs...> vals(std::forward<Args>(args)...);
     void *ptrs[sizeof...(KArgs)];
     std::apply([&](auto &...e) {
@@ -522,11 +523,17 @@ cudaGraphNode_t add_kernel(cudaGraph_t g, const cudaGraphNode_t *dep, void (*ker
     p.func = (void *)kern;
     p.gridDim = dim3(grid > 0 ? grid : 1);
     p.blockDim = dim3(kThreads);
-    p.sharedMemBytes = 0;
+    p.sharedMemBytes = (unsigned)smem;
     p.kernelParams = ptrs;
     cudaGraphNode_t node;
     GB_CUDA(cudaGraphAddKernelNode(&node, g, dep, dep ? 1 : 0, &p));
     return node;
+}
+
+template <class... KArgs, class... Args>
+cudaGraphNode_t add_kernel(cudaGraph_t g, const cudaGraphNode_t *dep, void (*kern)(KArgs...), int grid,
+                           Args &&...args) {
+    return add_kernel_smem(g, dep, kern, grid, 0, std::forward<Args>(args)...);
 }
 
 cudaGraphNode_t add_while(cudaGraph_t g, const cudaGraphNode_t *dep, cudaGraphConditionalHandle h,
@@ -590,15 +597,24 @@ public:
         GB_CUDA(cudaMemsetAsync(y_out_.p, 0, y_out_.bytes, stream_));
         GB_CUDA(cudaMemsetAsync(z_out_.p, 0, z_out_.bytes, stream_));
         // launch geometry and reduction scratch
+        // dynamic shared memory of the pipelined row-block kernels
+        for (const void *k : {(const void *)k_pcg_p_t<T>, (const void *)k_pcg_kp<T>, (const void *)k_pcg_init<T>,
+                              (const void *)k_admm_update<T>, (const void *)k_spmv<T, T>})
+            GB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemT));
+        for (const void *k : {(const void *)k_check_a<T>, (const void *)k_check_b<T>, (const void *)k_spmv_dbl<T>})
+            GB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemD));
         // each kernel's grid: its items, capped at the CTAs that fit at once
-        gPt_ = grid_for_items(planA_.nitems, (const void *)k_pcg_p_t<T>);
-        gAdmm_ = grid_for_items(planA_.nitems, (const void *)k_admm_update<T>);
-        gCa_ = grid_for_items(planA_.nitems, (const void *)k_check_a<T>);
-        gKp_ = grid_for_items(planPAt_.nitems, (const void *)k_pcg_kp<T>);
-        gInit_ = grid_for_items(planPAt_.nitems, (const void *)k_pcg_init<T>);
-        gCb_ = grid_for_items(planPAt_.nitems, (const void *)k_check_b<T>);
-        gridN_ = std::max(1, std::min(grid_for_n(std::max(n, m)), device_sm_count() * 8));
-        const int maxgrid = std::max({gPt_, gAdmm_, gCa_, gKp_, gInit_, gCb_, gridN_});
+        gPt_ = grid_for_items(planA_.nitems, (const void *)k_pcg_p_t<T>, kSmemT);
+        gAdmm_ = grid_for_items(planA_.nitems, (const void *)k_admm_update<T>, kSmemT);
+        gCa_ = grid_for_items(planA_.nitems, (const void *)k_check_a<T>, kSmemD);
+        gKp_ = grid_for_items(planPAt_.nitems, (const void *)k_pcg_kp<T>, kSmemT);
+        gInit_ = grid_for_items(planPAt_.nitems, (const void *)k_pcg_init<T>, kSmemT);
+        gCb_ = grid_for_items(planPAt_.nitems, (const void *)k_check_b<T>, kSmemD);
+        // vector kernels: about 4 elements per thread
+        const int cap = device_sm_count() * 8;
+        gridVec_ = std::max(1, std::min(grid_for_n(n, kThreads * 4), cap));
+        gridN_ = std::max(1, std::min(grid_for_n(std::max(n, m), kThreads * 4), cap));
+        const int maxgrid = std::max({gPt_, gAdmm_, gCa_, gKp_, gInit_, gCb_, gridN_, gridVec_});
         partials_.alloc(sizeof(double) * (size_t)maxgrid * 8);
         // status block
         Status h;
@@ -666,6 +682,7 @@ public:
         solve_ms_ = ms;
         Status h = read_status();
         last_ = h;
+        if (h.device_error) fail(GBOSQP_ERR_DEVICE_TIMEOUT, "a device wait for a bulk copy timed out");
         solve_launches = g_launches - before;
         if (exec_) {
             // kernels executed by the graph: reset, output, per iteration
@@ -785,7 +802,7 @@ public:
             // FP64 output through a double staging vector
             DevBuf yy(sizeof(double) * std::max(nout, 1));
             CsrDev<T> M = csr(pl, val);
-            const int g = grid_for_items(pl.nitems, (const void *)k_spmv_dbl<T>);
+            const int g = grid_for_items(pl.nitems, (const void *)k_spmv_dbl<T>, kSmemD);
             k_spmv_d(M, xT.as<T>(), yy.as<double>(), g);
             GB_CUDA(cudaMemcpyAsync(y, yy.p, sizeof(double) * nout, cudaMemcpyDeviceToHost, stream_));
         } else {
@@ -932,28 +949,39 @@ public:
         GB_CUDA(cudaMemcpyAsync(save_zt.p, zt_.p, zt_.bytes, cudaMemcpyDeviceToDevice, stream_));
         auto one = [&]() {
             switch (kernel) {
-                case GBOSQP_K_PCG_DIRECTION: launch(k_pcg_p_t<T>, gPt_, kThreads, stream_, csrA(), v, (const Status *)st); break;
-                case GBOSQP_K_PCG_KAPPLY: launch(k_pcg_kp<T>, gKp_, kThreads, stream_, csrPAt(), v, st, partials_.as<double>()); break;
-                case GBOSQP_K_PCG_UPDATE: launch(k_pcg_update<T>, gridN_, kThreads, stream_, v, st, partials_.as<double>(), (cudaGraphConditionalHandle)0, 0); break;
-                case GBOSQP_K_PCG_INIT: launch(k_pcg_init<T>, gInit_, kThreads, stream_, csrPAt(), v, st, partials_.as<double>(), (cudaGraphConditionalHandle)0, 0); break;
-                case GBOSQP_K_ADMM_UPDATE: launch(k_admm_update<T>, gAdmm_, kThreads, stream_, csrA(), v, st); break;
-                case GBOSQP_K_CHECK_A: launch(k_check_a<T>, gCa_, kThreads, stream_, csrA(), v, st, partials_.as<double>()); break;
-                case GBOSQP_K_CHECK_B: launch(k_check_b<T>, gCb_, kThreads, stream_, csrPAt(), v, st, partials_.as<double>(), policy(), (cudaGraphConditionalHandle)0, 0); break;
+                case GBOSQP_K_PCG_DIRECTION: launch_smem(k_pcg_p_t<T>, gPt_, kThreads, kSmemT, stream_, csrA(), v, (const Status *)st); break;
+                case GBOSQP_K_PCG_KAPPLY: launch_smem(k_pcg_kp<T>, gKp_, kThreads, kSmemT, stream_, csrPAt(), v, st, partials_.as<double>()); break;
+                case GBOSQP_K_PCG_UPDATE: launch(k_pcg_update<T>, gridVec_, kThreads, stream_, v, st, partials_.as<double>(), (cudaGraphConditionalHandle)0, 0); break;
+                case GBOSQP_K_PCG_INIT: launch_smem(k_pcg_init<T>, gInit_, kThreads, kSmemT, stream_, csrPAt(), v, st, partials_.as<double>(), (cudaGraphConditionalHandle)0, 0); break;
+                case GBOSQP_K_ADMM_UPDATE: launch_smem(k_admm_update<T>, gAdmm_, kThreads, kSmemT, stream_, csrA(), v, st); break;
+                case GBOSQP_K_CHECK_A: launch_smem(k_check_a<T>, gCa_, kThreads, kSmemD, stream_, csrA(), v, st, partials_.as<double>()); break;
+                case GBOSQP_K_CHECK_B: launch_smem(k_check_b<T>, gCb_, kThreads, kSmemD, stream_, csrPAt(), v, st, partials_.as<double>(), policy(), (cudaGraphConditionalHandle)0, 0); break;
                 default: fail(GBOSQP_ERR_INVALID_ARG, "unknown kernel selector");
             }
         };
         one();  // warm-up
+        GB_CUDA(cudaStreamSynchronize(stream_));
+        // time a graph of `reps` launches, so that host launch cost is excluded
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        GB_CUDA(cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal));
+        for (int i = 0; i < reps; ++i) one();
+        GB_CUDA(cudaStreamEndCapture(stream_, &g));
+        GB_CUDA(cudaGraphInstantiate(&ge, g, 0));
+        GB_CUDA(cudaGraphLaunch(ge, stream_));
         cudaEvent_t e0, e1;
         GB_CUDA(cudaEventCreate(&e0));
         GB_CUDA(cudaEventCreate(&e1));
         GB_CUDA(cudaEventRecord(e0, stream_));
-        for (int i = 0; i < reps; ++i) one();
+        GB_CUDA(cudaGraphLaunch(ge, stream_));
         GB_CUDA(cudaEventRecord(e1, stream_));
         GB_CUDA(cudaEventSynchronize(e1));
         float ms = 0.f;
         GB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
+        cudaGraphExecDestroy(ge);
+        cudaGraphDestroy(g);
         GB_CUDA(cudaMemcpyAsync(xy_.p, save_xy.p, xy_.bytes, cudaMemcpyDeviceToDevice, stream_));
         GB_CUDA(cudaMemcpyAsync(xt_.p, save_xt.p, xt_.bytes, cudaMemcpyDeviceToDevice, stream_));
         GB_CUDA(cudaMemcpyAsync(z_.p, save_z.p, z_.bytes, cudaMemcpyDeviceToDevice, stream_));
@@ -971,7 +999,7 @@ private:
 
     DevBuf convert(DevBuf &&src, long long count) {
         if (sizeof(T) == sizeof(double)) return std::move(src);
-        DevBuf out(sizeof(T) * std::max<long long>(count, 1));
+        DevBuf out(sizeof(T) * (count + 8));  // bulk copies may read 3 past the end
         if (count) launch(k_from_double<T>, ceil_div(count, 256), 256, stream_, src.as<double>(), out.as<T>(), count);
         GB_CUDA(cudaGetLastError());
         GB_CUDA(cudaStreamSynchronize(stream_));
@@ -1010,6 +1038,7 @@ private:
         M.longrows = pl.longrows.template as<LongRow>();
         M.lr_count = pl.count.template as<int>();
         M.lr_part = pl.part.template as<double>();
+        M.err = &(st_.template as<Status>()->device_error);
         return M;
     }
     CsrDev<T> csrA() const { return csr(planA_, A_val_.as<T>()); }
@@ -1049,33 +1078,33 @@ private:
     }
 
     void spmv_dev(const DevPlan &pl, const T *val, const T *x, T *y, T alpha) {
-        const int g = grid_for_items(pl.nitems, (const void *)k_spmv<T, T>);
-        launch(k_spmv<T, T>, g, kThreads, stream_, csr(pl, val), x, y, alpha);
+        const int g = grid_for_items(pl.nitems, (const void *)k_spmv<T, T>, kSmemT);
+        launch_smem(k_spmv<T, T>, g, kThreads, kSmemT, stream_, csr(pl, val), x, y, alpha);
         GB_CUDA(cudaGetLastError());
     }
     void k_spmv_d(CsrDev<T> M, const T *x, double *y, int g) {
-        launch(k_spmv_dbl<T>, g, kThreads, stream_, M, x, y);
+        launch_smem(k_spmv_dbl<T>, g, kThreads, kSmemD, stream_, M, x, y);
         GB_CUDA(cudaGetLastError());
     }
 
     // ---- host-driven launches (same kernels as the graph)
     void launch_init(const Vecs<T> &v, Status *st, cudaGraphConditionalHandle h, int use_h) {
-        launch(k_pcg_init<T>, gInit_, kThreads, stream_, csrPAt(), v, st, partials_.as<double>(), h, use_h);
+        launch_smem(k_pcg_init<T>, gInit_, kThreads, kSmemT, stream_, csrPAt(), v, st, partials_.as<double>(), h, use_h);
         GB_CUDA(cudaGetLastError());
     }
     void launch_step(const Vecs<T> &v, Status *st, cudaGraphConditionalHandle h, int use_h) {
-        launch(k_pcg_p_t<T>, gPt_, kThreads, stream_, csrA(), v, st);
-        launch(k_pcg_kp<T>, gKp_, kThreads, stream_, csrPAt(), v, st, partials_.as<double>());
-        launch(k_pcg_update<T>, gridN_, kThreads, stream_, v, st, partials_.as<double>(), h, use_h);
+        launch_smem(k_pcg_p_t<T>, gPt_, kThreads, kSmemT, stream_, csrA(), v, st);
+        launch_smem(k_pcg_kp<T>, gKp_, kThreads, kSmemT, stream_, csrPAt(), v, st, partials_.as<double>());
+        launch(k_pcg_update<T>, gridVec_, kThreads, stream_, v, st, partials_.as<double>(), h, use_h);
         GB_CUDA(cudaGetLastError());
     }
     void launch_admm(const Vecs<T> &v, Status *st) {
-        launch(k_admm_update<T>, gAdmm_, kThreads, stream_, csrA(), v, st);
+        launch_smem(k_admm_update<T>, gAdmm_, kThreads, kSmemT, stream_, csrA(), v, st);
         GB_CUDA(cudaGetLastError());
     }
     void launch_check(const Vecs<T> &v, Status *st, cudaGraphConditionalHandle h, int use_h) {
-        launch(k_check_a<T>, gCa_, kThreads, stream_, csrA(), v, st, partials_.as<double>());
-        launch(k_check_b<T>, gCb_, kThreads, stream_, csrPAt(), v, st, partials_.as<double>(), policy(), h, use_h);
+        launch_smem(k_check_a<T>, gCa_, kThreads, kSmemD, stream_, csrA(), v, st, partials_.as<double>());
+        launch_smem(k_check_b<T>, gCb_, kThreads, kSmemD, stream_, csrPAt(), v, st, partials_.as<double>(), policy(), h, use_h);
         GB_CUDA(cudaGetLastError());
     }
     void launch_rho(const Vecs<T> &v, Status *st) {
@@ -1121,16 +1150,16 @@ private:
         for (int s = 0; s < s_.check_every; ++s) {
             cudaGraphConditionalHandle hP;
             GB_CUDA(cudaGraphConditionalHandleCreate(&hP, body, 0, 0));
-            cudaGraphNode_t ni = add_kernel(body, prev ? &prev : nullptr, k_pcg_init<T>, gInit_, PAt, v, st, part, hP, 1);
+            cudaGraphNode_t ni = add_kernel_smem(body, prev ? &prev : nullptr, k_pcg_init<T>, gInit_, kSmemT, PAt, v, st, part, hP, 1);
             cudaGraph_t pbody;
             cudaGraphNode_t nw = add_while(body, &ni, hP, &pbody);
-            cudaGraphNode_t a = add_kernel(pbody, nullptr, k_pcg_p_t<T>, gPt_, A, v, (const Status *)st);
-            cudaGraphNode_t b = add_kernel(pbody, &a, k_pcg_kp<T>, gKp_, PAt, v, st, part);
-            add_kernel(pbody, &b, k_pcg_update<T>, gridN_, v, st, part, hP, 1);
-            prev = add_kernel(body, &nw, k_admm_update<T>, gAdmm_, A, v, st);
+            cudaGraphNode_t a = add_kernel_smem(pbody, nullptr, k_pcg_p_t<T>, gPt_, kSmemT, A, v, (const Status *)st);
+            cudaGraphNode_t b = add_kernel_smem(pbody, &a, k_pcg_kp<T>, gKp_, kSmemT, PAt, v, st, part);
+            add_kernel(pbody, &b, k_pcg_update<T>, gridVec_, v, st, part, hP, 1);
+            prev = add_kernel_smem(body, &nw, k_admm_update<T>, gAdmm_, kSmemT, A, v, st);
         }
-        cudaGraphNode_t ca = add_kernel(body, &prev, k_check_a<T>, gCa_, A, v, st, part);
-        cudaGraphNode_t cb = add_kernel(body, &ca, k_check_b<T>, gCb_, PAt, v, st, part, policy(), hA, 1);
+        cudaGraphNode_t ca = add_kernel_smem(body, &prev, k_check_a<T>, gCa_, kSmemD, A, v, st, part);
+        cudaGraphNode_t cb = add_kernel_smem(body, &ca, k_check_b<T>, gCb_, kSmemD, PAt, v, st, part, policy(), hA, 1);
         add_kernel(body, &cb, k_rho_apply<T>, gridN_, v, (const Status *)st);
         GB_CUDA(cudaGraphInstantiate(&exec_, graph_, 0));
     }
@@ -1173,7 +1202,9 @@ private:
     DevBuf x_out_, y_out_, z_out_;
     DevBuf partials_, st_, st2_, policy_;
     DevPlan planA_, planPAt_;
-    int gPt_ = 1, gAdmm_ = 1, gCa_ = 1, gKp_ = 1, gInit_ = 1, gCb_ = 1, gridN_ = 1;
+    int gPt_ = 1, gAdmm_ = 1, gCa_ = 1, gKp_ = 1, gInit_ = 1, gCb_ = 1, gridN_ = 1, gridVec_ = 1;
+    static constexpr size_t kSmemT = rowblock_smem<T, T>();
+    static constexpr size_t kSmemD = rowblock_smem<T, double>();
     cudaGraph_t graph_ = nullptr;
     cudaGraphExec_t exec_ = nullptr;
     float solve_ms_ = 0.f;
