@@ -268,10 +268,12 @@ int gbosqp_check(gbosqp_handle *h, double out[GBOSQP_CHECK_FIELDS]);
 #define GBOSQP_K_CHECK_A 5        /* ||Ax - z|| etc., FP64 accumulation (SpMV A)        */
 #define GBOSQP_K_CHECK_B 6        /* ||Px + q + A'y|| etc., FP64 (SpMV [P A'])          */
 
-/* Time `reps` back-to-back launches of one solve kernel, in the launch
- * configuration the solve uses, on the handle's current vectors: the
- * launches are captured into one CUDA graph on the handle's stream and the
- * graph launch is timed with CUDA events (so host launch cost is excluded).
+/* Time `reps` launches of one solve kernel, in the launch configuration the
+ * solve uses, on the handle's current vectors, each after a write of twice
+ * the L2 size (so the matrix comes from HBM, as inside a solve): the
+ * sequence is captured into a CUDA graph on the handle's stream and timed
+ * with CUDA events, minus the same graph without the kernel (host launch
+ * cost and the flushes excluded).
  * A private copy of the scalar state is used and the iterates are restored,
  * so the next solve is unaffected.  Writes the mean duration in ms. */
 int gbosqp_bench_kernel(gbosqp_handle *h, int kernel, int32_t reps, double *avg_ms);

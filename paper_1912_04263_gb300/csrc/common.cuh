@@ -243,10 +243,30 @@ __device__ __forceinline__ void grid_finish(Red<NS, NM> &red, double *partials, 
 
 // ------------------------------------------------------ row-block SpMV core
 
+// Exact float -> double by rebuilding the IEEE-754 fields (sign, exponent
+// rebiased from 127 to 1023, 23-bit significand shifted into the 52-bit
+// one) with integer operations; zero, subnormal, inf and NaN inputs take
+// the ordinary conversion.  Keeps the conversion off the FP64 pipe, which
+// is narrow on this GPU, in the FP64-accumulating SpMVs.
+__device__ __forceinline__ double f2d_exact(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned ex = (u >> 23) & 0xffu;
+    if (ex == 0u || ex == 0xffu) return (double)f;
+    const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                 ((unsigned long long)(ex + (1023u - 127u)) << 52) |
+                                 ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)d);
+}
+
+template <class Acc, class T>
+__device__ __forceinline__ Acc to_acc(T v) { return Acc(v); }
+template <>
+__device__ __forceinline__ double to_acc<double, float>(float v) { return f2d_exact(v); }
+
 // Row reduction of one block item with lane groups of G threads.  sprod
 // holds the item's products; epi.row(r, s1, s2, red) consumes each row.
 template <int G, bool SPLIT, class Acc, class T, class Epi, class RedT>
-__device__ __forceinline__ void reduce_rows(const CsrDev<T> &M, const Item &it, const Acc *sprod, Epi &epi,
+__device__ __forceinline__ void reduce_rows(const CsrDev<T> &M, const Item &it, const T *sprod, Epi &epi,
                                             RedT &red) {
     const int lane_g = threadIdx.x & (G - 1);
     const int grp = threadIdx.x / G;
@@ -262,10 +282,10 @@ __device__ __forceinline__ void reduce_rows(const CsrDev<T> &M, const Item &it, 
             if (SPLIT) {
                 const int sp = __ldg(M.pend + r) - it.k0;
                 for (int e = a + lane_g; e < b; e += G) {
-                    if (e < sp) s1 += sprod[e]; else s2 += sprod[e];
+                    if (e < sp) s1 += to_acc<Acc>(sprod[e]); else s2 += to_acc<Acc>(sprod[e]);
                 }
             } else {
-                for (int e = a + lane_g; e < b; e += G) s1 += sprod[e];
+                for (int e = a + lane_g; e < b; e += G) s1 += to_acc<Acc>(sprod[e]);
             }
         }
         if (G > 1) {
@@ -279,10 +299,35 @@ __device__ __forceinline__ void reduce_rows(const CsrDev<T> &M, const Item &it, 
     }
 }
 
-// Dynamic shared memory of a row-block kernel (the products of one item).
+// Dynamic shared memory of a row-block kernel (the products of one item,
+// kept in the working precision; rows accumulate them in Acc).
 template <class T, class Acc>
 constexpr size_t rowblock_smem() {
-    return (size_t)kCap * sizeof(Acc);
+    return (size_t)kCap * sizeof(T);
+}
+
+// Bulk prefetch of [p, p + bytes) into L2 by the copy engine (sm_90+); p
+// 16-byte aligned and bytes a multiple of 16.
+__device__ __forceinline__ void l2_prefetch(const void *p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Items ahead of the current one whose ranges are prefetched into L2.
+#ifndef GB_L2_AHEAD
+#define GB_L2_AHEAD 3
+#endif
+constexpr int kL2Ahead = GB_L2_AHEAD;
+
+// Prefetch the value and column ranges of an item into L2, rounded out to
+// 16-byte boundaries (the arrays carry 8 elements of padding).
+template <class T>
+__device__ __forceinline__ void prefetch_item(const CsrDev<T> &M, const Item &it) {
+    const int k0a = it.k0 & ~3;
+    const int k1a = (it.k1 + 3) & ~3;
+    if (k1a > k0a) {
+        l2_prefetch(M.val + k0a, (unsigned)((k1a - k0a) * sizeof(T)));
+        l2_prefetch(M.col + k0a, (unsigned)((k1a - k0a) * sizeof(int)));
+    }
 }
 
 // Load the value/column range of an item into registers (streaming loads:
@@ -302,8 +347,10 @@ __device__ __forceinline__ void load_item(const CsrDev<T> &M, const Item &it, T 
 
 // Process the contiguous range of items assigned to this CTA.  Each step
 // prefetches the next item's values and columns into registers, then
-// multiplies the current item by the gathered vector (into shared memory)
-// and reduces its rows with lane groups sized to the mean row length.
+// multiplies the current item by the gathered vector in the working
+// precision (into shared memory) and reduces its rows with lane groups sized
+// to the mean row length, accumulating in Acc (FP64 for the termination
+// check: FP32 products summed in FP64).
 // Consecutive pieces of a long row accumulate per thread and are reduced
 // once; a long row that crosses a CTA boundary is combined by the last of
 // its contributors, in CTA order.  gather(c) returns the vector entry for
@@ -311,18 +358,21 @@ __device__ __forceinline__ void load_item(const CsrDev<T> &M, const Item &it, T 
 template <class Acc, bool SPLIT, class T, class Gather, class Epi, class RedT>
 __device__ __forceinline__ bool run_items(const CsrDev<T> &M, const Gather &gather, Epi &epi, RedT &red) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Acc *sprod = reinterpret_cast<Acc *>(smem_raw);
+    T *sprod = reinterpret_cast<T *>(smem_raw);
     __shared__ Acc wsum[2][kWarps];
     const int Q = (M.nitems + (int)gridDim.x - 1) / (int)gridDim.x;
     const int i0 = (int)blockIdx.x * Q;
     const int i1 = min(M.nitems, i0 + Q);
     T va[kPerThread], vb[kPerThread];
     int ca[kPerThread], cb[kPerThread];
+    if (threadIdx.x == 0)
+        for (int j = i0 + 1; j <= i0 + kL2Ahead && j < i1; ++j) prefetch_item(M, M.items[j]);
     if (i0 < i1) load_item(M, M.items[i0], va, ca);
     Acc ps1 = Acc(0), ps2 = Acc(0);  // running sums of a long row's pieces
     for (int itx = i0; itx < i1; ++itx) {
         const Item it = M.items[itx];
         const bool has_next = itx + 1 < i1;
+        if (threadIdx.x == 0 && itx + 1 + kL2Ahead < i1) prefetch_item(M, M.items[itx + 1 + kL2Ahead]);
         Item nx;
         if (has_next) {
             nx = M.items[itx + 1];
@@ -333,7 +383,7 @@ __device__ __forceinline__ bool run_items(const CsrDev<T> &M, const Gather &gath
 #pragma unroll
             for (int u = 0; u < kPerThread; ++u) {
                 const int e = u * kThreads + threadIdx.x;
-                if (e < nnz) sprod[e] = Acc(va[u]) * gather(ca[u]);
+                if (e < nnz) sprod[e] = va[u] * gather(ca[u]);
             }
             __syncthreads();
             const int R = it.r1 - it.r0;
@@ -351,7 +401,7 @@ __device__ __forceinline__ bool run_items(const CsrDev<T> &M, const Gather &gath
             for (int u = 0; u < kPerThread; ++u) {
                 const int e = u * kThreads + threadIdx.x;
                 if (e < nnz) {
-                    const Acc pr = Acc(va[u]) * gather(ca[u]);
+                    const Acc pr = to_acc<Acc>(va[u] * gather(ca[u]));
                     if (!SPLIT || e < sp) ps1 += pr; else ps2 += pr;
                 }
             }

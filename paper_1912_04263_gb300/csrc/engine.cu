@@ -221,25 +221,27 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : 2) k_p
     grid_finish<1, 0>(red, partials, &st->tickets[kTkK2], fin);
 }
 
-// x~ += a p; r += a Kp; yv = M^{-1} r; p_prev = p; r'yv; ||r||_inf; beta
+// x~ += a p; r += a Kp; yv = M^{-1} r; p_prev = p; r'yv; ||r||_inf; beta.
+// The vector updates run in the working precision; r'yv accumulates the
+// exact products in FP64.
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_pcg_update(Vecs<T> v, Status *st, double *partials,
                                                          cudaGraphConditionalHandle hP, int use_h) {
-    const double a = st->alpha_cg;
+    const T a = T(st->alpha_cg);
     const int n = v.n;
     Red<1, 1> red;
     red.zero();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const T p = v.pt[i];
-        const T x = T((double)v.xt[i] + a * (double)p);
-        const T r = T((double)v.r[i] + a * (double)v.kp[i]);
+        const T x = v.xt[i] + a * p;
+        const T r = v.r[i] + a * v.kp[i];
         const T y = v.minv[i] * r;
         v.xt[i] = x;
         v.r[i] = r;
         v.yv[i] = y;
         v.pc[i] = p;
         red.s[0] += (double)r * (double)y;
-        red.m[0] = nanmax(red.m[0], fabs((double)r));
+        red.m[0] = nanmax(red.m[0], (double)fabs(r));
     }
     auto fin = [&](const Red<1, 1> &t) {
         if (threadIdx.x != 0) return;
@@ -311,11 +313,11 @@ struct EpiCheckA {
 };
 
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_check_a(CsrDev<T> A, Vecs<T> v, Status *st, double *partials) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_check_a(CsrDev<T> A, Vecs<T> v, Status *st, double *partials) {
     EpiCheckA<T> epi{v};
     Red<0, 6> red;
     red.zero();
-    run_items<double, false>(A, GatherVec<T, double>{v.xy}, epi, red);
+    run_items<double, false>(A, GatherVec<T, T>{v.xy}, epi, red);
     auto fin = [&](const Red<0, 6> &t) {
         if (threadIdx.x == 0)
             for (int i = 0; i < 6; ++i) st->c1[i] = t.m[i];
@@ -342,14 +344,14 @@ struct EpiCheckB {
 };
 
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_check_b(CsrDev<T> PAt, Vecs<T> v, Status *st, double *partials,
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_check_b(CsrDev<T> PAt, Vecs<T> v, Status *st, double *partials,
                                                       PolicyDev pol, cudaGraphConditionalHandle hA, int use_h) {
     __shared__ double new_rho_sh;
     __shared__ int decide_sh;
     EpiCheckB<T> epi{v};
     Red<1, 6> red;
     red.zero();
-    run_items<double, true>(PAt, GatherVec<T, double>{v.xy}, epi, red);
+    run_items<double, true>(PAt, GatherVec<T, T>{v.xy}, epi, red);
     auto fin = [&](const Red<1, 6> &t) {
         if (threadIdx.x == 0) {
             const double cinv = st->cinv;
@@ -452,7 +454,7 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) k_spmv_dbl(CsrDev<T> M, const T *x, double *y) {
     EpiStore<double, double> epi{y, 1.0};
     Red<0, 0> red;
-    run_items<double, false>(M, GatherVec<T, double>{x}, epi, red);
+    run_items<double, false>(M, GatherVec<T, T>{x}, epi, red);
 }
 
 // t0 = rho (zt - z) + y
@@ -612,7 +614,7 @@ public:
         gCb_ = grid_for_items(planPAt_.nitems, (const void *)k_check_b<T>, kSmemD);
         // vector kernels: about 4 elements per thread
         const int cap = device_sm_count() * 8;
-        gridVec_ = std::max(1, std::min(grid_for_n(n, kThreads * 4), cap));
+        gridVec_ = std::max(1, std::min(grid_for_n(n, kThreads), cap));
         gridN_ = std::max(1, std::min(grid_for_n(std::max(n, m), kThreads * 4), cap));
         const int maxgrid = std::max({gPt_, gAdmm_, gCa_, gKp_, gInit_, gCb_, gridN_, gridVec_});
         partials_.alloc(sizeof(double) * (size_t)maxgrid * 8);
@@ -961,27 +963,41 @@ public:
         };
         one();  // warm-up
         GB_CUDA(cudaStreamSynchronize(stream_));
-        // time a graph of `reps` launches, so that host launch cost is excluded
-        cudaGraph_t g = nullptr;
-        cudaGraphExec_t ge = nullptr;
-        GB_CUDA(cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal));
-        for (int i = 0; i < reps; ++i) one();
-        GB_CUDA(cudaStreamEndCapture(stream_, &g));
-        GB_CUDA(cudaGraphInstantiate(&ge, g, 0));
-        GB_CUDA(cudaGraphLaunch(ge, stream_));
-        cudaEvent_t e0, e1;
-        GB_CUDA(cudaEventCreate(&e0));
-        GB_CUDA(cudaEventCreate(&e1));
-        GB_CUDA(cudaEventRecord(e0, stream_));
-        GB_CUDA(cudaGraphLaunch(ge, stream_));
-        GB_CUDA(cudaEventRecord(e1, stream_));
-        GB_CUDA(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        GB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        cudaGraphExecDestroy(ge);
-        cudaGraphDestroy(g);
+        // L2 is flushed before every timed launch (a write of twice the L2
+        // size): graph A = reps x [flush, kernel], graph B = reps x [flush];
+        // the kernel time is (A - B) / reps, host launch cost excluded
+        int dev = 0, l2 = 0;
+        GB_CUDA(cudaGetDevice(&dev));
+        GB_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+        const size_t fbytes = 2 * (size_t)std::max(l2, 1 << 20);
+        DevBuf flush(fbytes);
+        auto time_graph = [&](bool with_kernel) {
+            cudaGraph_t g = nullptr;
+            cudaGraphExec_t ge = nullptr;
+            GB_CUDA(cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal));
+            for (int i = 0; i < reps; ++i) {
+                GB_CUDA(cudaMemsetAsync(flush.p, i & 0xff, fbytes, stream_));
+                if (with_kernel) one();
+            }
+            GB_CUDA(cudaStreamEndCapture(stream_, &g));
+            GB_CUDA(cudaGraphInstantiate(&ge, g, 0));
+            GB_CUDA(cudaGraphLaunch(ge, stream_));
+            cudaEvent_t e0, e1;
+            GB_CUDA(cudaEventCreate(&e0));
+            GB_CUDA(cudaEventCreate(&e1));
+            GB_CUDA(cudaEventRecord(e0, stream_));
+            GB_CUDA(cudaGraphLaunch(ge, stream_));
+            GB_CUDA(cudaEventRecord(e1, stream_));
+            GB_CUDA(cudaEventSynchronize(e1));
+            float t = 0.f;
+            GB_CUDA(cudaEventElapsedTime(&t, e0, e1));
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            cudaGraphExecDestroy(ge);
+            cudaGraphDestroy(g);
+            return t;
+        };
+        const float ms = std::max(0.f, time_graph(true) - time_graph(false));
         GB_CUDA(cudaMemcpyAsync(xy_.p, save_xy.p, xy_.bytes, cudaMemcpyDeviceToDevice, stream_));
         GB_CUDA(cudaMemcpyAsync(xt_.p, save_xt.p, xt_.bytes, cudaMemcpyDeviceToDevice, stream_));
         GB_CUDA(cudaMemcpyAsync(z_.p, save_z.p, z_.bytes, cudaMemcpyDeviceToDevice, stream_));

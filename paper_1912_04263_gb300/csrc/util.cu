@@ -52,9 +52,17 @@ int grid_for_items(int nitems, const void *kernel, int smem_dynamic) {
 
 int grid_for_n(long long n, int threads) { return (int)std::max(1LL, (n + threads - 1) / threads); }
 
+// Lane-group width the kernels use for an item with mean row length avg
+// (must match the choice in run_items).
+static int group_width(long long avg) {
+    return avg >= 24 ? 32 : avg >= 12 ? 16 : avg >= 6 ? 8 : avg >= 3 ? 4 : 1;
+}
+
 // Cut the rows into work items: runs of consecutive rows with at most kCap
-// nonzeros and at most kCap rows; a row longer than kCap becomes ceil(len /
-// kCap) pieces of nearly equal length, combined by the last piece.
+// nonzeros and few enough rows that the CTA's lane groups reduce them in at
+// most two rounds (rows x group width <= 2 x kThreads), so that items of
+// short rows cost about as much as items of long ones; a row longer than
+// kCap becomes ceil(len / kCap) pieces of nearly equal length.
 HostPlan build_plan(const std::vector<int> &rp) {
     HostPlan hp;
     const int nrows = (int)rp.size() - 1;
@@ -77,7 +85,9 @@ HostPlan build_plan(const std::vector<int> &rp) {
         long long tot = 0;
         while (r < nrows) {
             const long long l = (long long)rp[r + 1] - rp[r];
-            if (l > kCap || tot + l > kCap || r - r0 >= kCap) break;
+            if (l > kCap || tot + l > kCap) break;
+            const long long rows = r - r0 + 1;
+            if (rows > 1 && rows * group_width((tot + l) / rows) > 2LL * kThreads) break;
             tot += l;
             ++r;
         }
