@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "time-to-1e-3 solve & ADMM it/s (learned FP32 vs plain FP64); SpMV GB/s"
 WORKLOAD = "lasso_1000x100000"
-WORKLOAD_TEXT = ("Lasso QP (configs[1] shape): D 100000x1000 at 15% density N(0,1), "
+WORKLOAD_TEXT = ("Lasso QP: D 100000x1000 at 15% density N(0,1), "
                  "variables (x, y, t), n = m = 102000, eps_abs = eps_rel = 1e-3")
 HBM_FALLBACK_GBS = 6800.0
 

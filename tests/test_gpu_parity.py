@@ -428,7 +428,7 @@ def test_max_iter_status(gb):
 
 
 @pytest.mark.parametrize("seed", range(10))
-def test_configs0_random_fp64_ten_seeds(gb, seed):
+def test_random_100x1000_fp64_ten_seeds(gb, seed):
     """The plain-method FP64 workload (n = 100, m = 1000) on seeds 0-9:
     residuals within the rule; objective within 1e-3 of the tight oracle
     where the oracle's own 1e-3 solve gets there, else within the
