@@ -278,6 +278,31 @@ int gbosqp_check(gbosqp_handle *h, double out[GBOSQP_CHECK_FIELDS]);
  * so the next solve is unaffected.  Writes the mean duration in ms. */
 int gbosqp_bench_kernel(gbosqp_handle *h, int kernel, int32_t reps, double *avg_ms);
 
+/* y = M x, the same computation and kernel as gbosqp_spmv without FP64
+ * accumulation, for callers that cannot let the library allocate device
+ * memory during the call: real-time loops that must not take the
+ * allocator's latency (cudaMalloc/cudaFree can take milliseconds and
+ * cudaFree waits for the whole device), code recording a CUDA stream capture
+ * (a device-wide synchronisation would invalidate it), and hosts whose device
+ * memory is owned by another allocator.  The paper has no counterpart.
+ *
+ *   which  GBOSQP_MAT_A (x: n entries, y: m) or GBOSQP_MAT_PAT (x: n + m, y: n)
+ *   x, y   device arrays on the handle's device, of float on an FP32 handle
+ *          and double on an FP64 handle; caller-owned; may not overlap
+ *
+ * Allocates nothing: the scratch that combines the pieces of long rows is a
+ * fixed device array inside the library (2.5 MiB, resident on every device
+ * that loads the library until the process exits), which holds up to 131072
+ * work items and 131072 long rows per matrix; a larger matrix is rejected
+ * with GBOSQP_ERR_UNSUPPORTED.  The first call on each device looks up that
+ * array's device address; make that first call before any stream capture.
+ * Every call shares the array (its counters are cleared at the start of each
+ * call and it keeps the last call's partial sums), so calls that overlap on
+ * the GPU, from any thread or handle, race: serialise them.  The work is
+ * queued on the handle's stream and the call returns without waiting;
+ * synchronise that stream (or the device) before reading y. */
+int gbosqp_spmv_noalloc(gbosqp_handle *h, int which, const void *x, void *y);
+
 #ifdef __cplusplus
 }
 #endif

@@ -96,6 +96,7 @@ def lib():
         "gbosqp_admm_iterations": (i32, [_P, i32, _P]),
         "gbosqp_check": (i32, [_P, _P]),
         "gbosqp_bench_kernel": (i32, [_P, i32, i32, _P]),
+        "gbosqp_spmv_noalloc": (i32, [_P, i32, _P, _P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -305,6 +306,12 @@ def gbosqp_bench_kernel(h, kernel: int, reps: int) -> float:
     ms = ctypes.c_double()
     _check(h, lib().gbosqp_bench_kernel(h, int(kernel), int(reps), ctypes.byref(ms)))
     return ms.value
+
+
+def gbosqp_spmv_noalloc(h, which: int, x, y) -> None:
+    """y = M x on device tensors of the handle's working precision, without
+    any device allocation in the call (asynchronous on the handle's stream)."""
+    _check(h, lib().gbosqp_spmv_noalloc(h, int(which), x.data_ptr(), y.data_ptr()))
 
 
 CHECK_NAMES = ["r_prim", "r_dual", "eps_prim", "eps_dual", "r_prim_s", "r_dual_s", "norm_Ax_s", "norm_z_s",

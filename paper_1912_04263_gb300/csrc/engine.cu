@@ -1006,11 +1006,28 @@ public:
         return reps > 0 ? ms / reps : 0.0;
     }
 
+    void spmv_noalloc(int which, const void *x, void *y, double *part, int *count, long long max_items,
+                      long long max_long_rows) override {
+        const bool isA = which == GBOSQP_MAT_A;
+        const DevPlan &pl = isA ? planA_ : planPAt_;
+        if (pl.nitems > max_items || pl.nlong > max_long_rows)
+            fail(GBOSQP_ERR_UNSUPPORTED, "matrix needs " + std::to_string(pl.nitems) + " work items and " +
+                                             std::to_string(pl.nlong) + " long rows; the allocation-free SpMV holds at most " +
+                                             std::to_string(max_items) + " and " + std::to_string(max_long_rows));
+        CsrDev<T> M = csr(pl, isA ? A_val_.as<T>() : PAt_val_.as<T>());
+        M.lr_part = part;
+        M.lr_count = count;
+        if (pl.nlong > 0) GB_CUDA(cudaMemsetAsync(count, 0, sizeof(int) * (size_t)pl.nlong, stream_));
+        const int g = grid_for_items(pl.nitems, (const void *)k_spmv<T, T>, kSmemT);
+        launch_smem(k_spmv<T, T>, g, kThreads, kSmemT, stream_, M, static_cast<const T *>(x), static_cast<T *>(y), T(1));
+    }
+
 private:
     struct DevPlan {
         DevBuf items, longrows, count, part;
         int nitems = 0;
         int nrows = 0;
+        int nlong = 0;
     };
 
     DevBuf convert(DevBuf &&src, long long count) {
@@ -1026,6 +1043,7 @@ private:
         HostPlan hp = build_plan(rp);
         pl.nitems = (int)hp.items.size();
         pl.nrows = (int)rp.size() - 1;
+        pl.nlong = (int)hp.longrows.size();
         pl.items.alloc(sizeof(Item) * std::max<size_t>(hp.items.size(), 1));
         pl.longrows.alloc(sizeof(LongRow) * std::max<size_t>(hp.longrows.size(), 1));
         pl.count.alloc(sizeof(int) * std::max<size_t>(hp.longrows.size(), 1));

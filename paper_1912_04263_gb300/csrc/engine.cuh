@@ -47,6 +47,11 @@ public:
     virtual int admm_iterations(int k, int *pcg_per_iter) = 0;
     virtual void check(double *out) = 0;
     virtual double bench_kernel(int kernel, int reps) = 0;
+    // y = M x on device arrays of the working precision, with the long-row
+    // scratch supplied by the caller (part: 2 doubles per work item, count:
+    // one int per long row); allocates nothing.
+    virtual void spmv_noalloc(int which, const void *x, void *y, double *part, int *count, long long max_items,
+                              long long max_long_rows) = 0;
     int n = 0, m = 0;
     long long solve_launches = 0;
     long long nnzA = 0, nnzPAt = 0, nnzP = 0;
