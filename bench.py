@@ -35,6 +35,7 @@ WORKLOAD = "lasso_1000x100000"
 WORKLOAD_TEXT = ("Lasso QP: D 100000x1000 at 15% density N(0,1), "
                  "variables (x, y, t), n = m = 102000, eps_abs = eps_rel = 1e-3")
 HBM_FALLBACK_GBS = 6800.0
+POLICY_PATH = os.path.join(ROOT, "paper_1912_04263_gb300", "policy", "rho_policy.bin")
 
 
 def peaks():
@@ -177,11 +178,18 @@ def gpu_arm(args) -> None:
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.synchronize()
 
+    policy = None
+    if os.path.exists(POLICY_PATH) and args.policy == "learned":
+        policy = gb.load_policy(POLICY_PATH)
+
     def settings(prec):
         s = gb.default_settings(precision=prec, device=local)
         s.cuda_stream = stream.cuda_stream
         if args.loop == "host":
             s.loop_mode = gb.LOOP_HOST
+        if prec == gb.FP32 and policy is not None:
+            s.rho_policy = gb.RHO_LEARNED
+            s.policy_params = policy.ctypes.data
         return s
 
     def setup_device(prec):
@@ -325,7 +333,7 @@ def gpu_arm(args) -> None:
         "dtype": "f32 (f64 reductions)",
         "data": "synthetic",
         "config": {"workload": WORKLOAD_TEXT, "name": args.workload, "seed": args.seed, "n": n, "m": m,
-                   "nnz_A": int(A.nnz), "nnz_P": int(P.nnz), "precision": "fp32", "rho_policy": "ratio",
+                   "nnz_A": int(A.nnz), "nnz_P": int(P.nnz), "precision": "fp32", "rho_policy": "learned" if policy is not None else "ratio",
                    "step": "osqp_setup(device CSR) + osqp_solve + solution to device",
                    "l2": "no flush: each step streams >240 MB of matrices, above the 129 MB L2",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -338,7 +346,7 @@ def gpu_arm(args) -> None:
         "admm_it_per_s": iters / (solve_ms / 1000.0),
         "spmv_gbs": {k: round(v, 1) for k, v in gbs.items()},
         "kernel_ms": {k: round(v, 5) for k, v in k_ms.items()},
-        "plain_fp64": {"time_to_1e3_s": fp64_step / 1000.0, "status": sorted(set(int(s) for s in fp64_stats)),
+        "plain_fp64": {"rho_policy": "ratio", "time_to_1e3_s": fp64_step / 1000.0, "status": sorted(set(int(s) for s in fp64_stats)),
                        "admm_iters": med("iters", fp64_infos), "pcg_iters": med("pcg_iters", fp64_infos),
                        "solve_ms": med("solve_ms", fp64_infos)},
         "roofline": {"bound": "hbm", "kernel": dominant, "achieved": round(gbs[dominant], 1), "peak": hbm,
@@ -397,6 +405,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-leg", action="store_true")
     ap.add_argument("--lean", action="store_true", help="warm-up steps then one step, minimal output (profiling)")
+    ap.add_argument("--policy", default="learned", choices=["learned", "ratio"],
+                    help="rho rule of the FP32 form (learned: the committed trained policy, if present)")
     ap.add_argument("--loop", default="graph", choices=["graph", "host"],
                     help="host: the same kernels driven by a host loop (profilers cannot attribute kernel "
                          "nodes inside graphs with conditional nodes)")

@@ -128,7 +128,9 @@ typedef struct {
                                    GBOSQP_POLICY_PARAMS floats) or NULL    */
 } gbosqp_settings;
 
-/* Layout of the learned-policy parameter vector (see gbosqp_policy.h). */
+/* Learned-policy parameter vector (FP32): feature mean (4), feature std (4),
+ * W1 (64x4, row major), b1 (64), W2 (64x64), b2 (64), W3 (2x64), b3 (2),
+ * then log-multiplier clamp, lambda_min, lambda_max, use_lambda (1/0). */
 #define GBOSQP_POLICY_PARAMS 4622
 
 typedef struct {
@@ -258,6 +260,40 @@ int gbosqp_admm_iterations(gbosqp_handle *h, int32_t k, int32_t *pcg_per_iter);
  * r_prim, r_dual, ||Ax||, ||z||, ||Px||, ||A'y||, ||q|| (used by the rho
  * rule and the PCG tolerance), the objective, and 4 reserved zeros. */
 int gbosqp_check(gbosqp_handle *h, double out[GBOSQP_CHECK_FIELDS]);
+
+/* ---- learned rho policy (not in the paper) ----------------------------- *
+ * A 4-64-64-2 MLP (ReLU) proposes, at every rho decision, a log multiplier
+ * for rho (output 0, clamped) and a log factor for the PCG tolerance weight
+ * lambda (output 1, used when the last parameter is 1).  Its features are
+ * log ||r_prim||, log ||r_dual|| (scaled problem), log rho and
+ * log(1 + PCG steps since the last decision); it sees (f - mean) / std.
+ * Operands are rounded to BF16 (weights, inputs, hidden activations and, in
+ * training, the back-propagated signals); products accumulate in FP32.
+ * These calls take host arrays, allocate device memory for the call and
+ * synchronise. */
+
+/* out (batch x 2) = network(features (batch x 4, raw)) with the device code
+ * the solver uses for its decisions. */
+int gbosqp_policy_forward(const float *params, const float *features, int32_t batch, float *out);
+
+/* Gradient of loss = sum_k w_k (o_k - t_k)^2 / (2n) over the n samples
+ * (features n x 4 raw, targets and weights n x 2) with respect to the
+ * weights and biases; grad has GBOSQP_POLICY_PARAMS entries (zero outside
+ * W1..b3).  loss may be NULL. */
+int gbosqp_mlp_grad(const float *params, const float *features, const float *targets, const float *weights,
+                    int32_t n, float *grad, float *loss);
+
+/* `steps` Adam steps (lr, beta1 0.9, beta2 0.999, eps 1e-8) on the weights
+ * and biases of params (updated in place), step s using the samples
+ * batches[s*batch .. s*batch+batch) (indices into the n samples).  Writes the
+ * loss of every step to loss_history (steps entries, may be NULL). */
+int gbosqp_mlp_train(float *params, const float *features, const float *targets, const float *weights, int32_t n,
+                     const int32_t *batches, int32_t steps, int32_t batch, float lr, float *loss_history);
+
+/* Set the PCG tolerance weight lambda of Section 5.3.4 for the following
+ * checks of a handle and the current PCG tolerance eps (> 0) until the next
+ * check (step-level call, e.g. for policy lookahead). */
+int gbosqp_set_pcg_lambda(gbosqp_handle *h, double lambda, double eps);
 
 /* Kernel selectors for gbosqp_bench_kernel. */
 #define GBOSQP_K_PCG_DIRECTION 0  /* p = -M^{-1}r + beta p, t = rho A p (SpMV A)        */

@@ -91,3 +91,37 @@ def adam_step(params, g, state, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
         vh = v / (1.0 - b2 ** t)
         params[k] = params[k] - lr * mh / (np.sqrt(vh) + eps)
     return params
+
+
+def grads_bf16(params: dict, X: np.ndarray, target, weight):
+    """The forward and backward pass with the rounding points of the BF16
+    kernels: weights, inputs, hidden activations and the back-propagated
+    signals (dL/do, and the two pre-activation gradients) rounded to BF16;
+    biases unrounded; everything else exact.  X is the normalised input."""
+    W1, W2, W3 = (bf16_round(params[k]) for k in ("W1", "W2", "W3"))
+    b1, b2, b3 = params["b1"], params["b2"], params["b3"]
+    x = bf16_round(X)
+    a1 = x @ W1.T + b1
+    h1 = bf16_round(np.maximum(a1, 0.0))
+    a2 = h1 @ W2.T + b2
+    h2 = bf16_round(np.maximum(a2, 0.0))
+    out = h2 @ W3.T + b3
+    loss, dout = loss_and_grad_out(out, target, weight)
+    dout = bf16_round(dout)
+    g = {"W3": dout.T @ h2, "b3": dout.sum(axis=0)}
+    d2 = bf16_round((dout @ W3) * (a2 > 0.0))
+    g["W2"] = d2.T @ h1
+    g["b2"] = d2.sum(axis=0)
+    d1 = bf16_round((d2 @ W2) * (a1 > 0.0))
+    g["W1"] = d1.T @ x
+    g["b1"] = d1.sum(axis=0)
+    return loss, g, out
+
+
+def forward_bf16(params: dict, X: np.ndarray):
+    """Inference with the BF16 rounding points of the device code."""
+    W1, W2, W3 = (bf16_round(params[k]) for k in ("W1", "W2", "W3"))
+    x = bf16_round(X)
+    h1 = bf16_round(np.maximum(x @ W1.T + params["b1"], 0.0))
+    h2 = bf16_round(np.maximum(h1 @ W2.T + params["b2"], 0.0))
+    return h2 @ W3.T + params["b3"]

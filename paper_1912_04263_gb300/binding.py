@@ -97,6 +97,10 @@ def lib():
         "gbosqp_check": (i32, [_P, _P]),
         "gbosqp_bench_kernel": (i32, [_P, i32, i32, _P]),
         "gbosqp_spmv_noalloc": (i32, [_P, i32, _P, _P]),
+        "gbosqp_policy_forward": (i32, [_P, _P, i32, _P]),
+        "gbosqp_mlp_grad": (i32, [_P, _P, _P, _P, i32, _P, _P]),
+        "gbosqp_mlp_train": (i32, [_P, _P, _P, _P, i32, _P, i32, i32, ctypes.c_float, _P]),
+        "gbosqp_set_pcg_lambda": (i32, [_P, dbl, dbl]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -312,6 +316,86 @@ def gbosqp_spmv_noalloc(h, which: int, x, y) -> None:
     """y = M x on device tensors of the handle's working precision, without
     any device allocation in the call (asynchronous on the handle's stream)."""
     _check(h, lib().gbosqp_spmv_noalloc(h, int(which), x.data_ptr(), y.data_ptr()))
+
+
+def _f32(a, shape=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    if shape is not None and a.shape != shape:
+        raise ValueError(f"expected shape {shape}, got {a.shape}")
+    return a
+
+
+def _rc(rc):
+    if rc != OK:
+        raise GbosqpError(rc, error_string(rc))
+
+
+def gbosqp_policy_forward(params, features) -> np.ndarray:
+    p = _f32(params, (POLICY_PARAMS,))
+    f = _f32(features)
+    f = f.reshape(-1, 4)
+    out = np.empty((f.shape[0], 2), np.float32)
+    _rc(lib().gbosqp_policy_forward(p.ctypes.data, f.ctypes.data, f.shape[0], out.ctypes.data))
+    return out
+
+
+def gbosqp_mlp_grad(params, features, targets, weights):
+    p = _f32(params, (POLICY_PARAMS,))
+    f = _f32(features).reshape(-1, 4)
+    n = f.shape[0]
+    t = _f32(targets, (n, 2))
+    w = _f32(weights, (n, 2))
+    g = np.zeros(POLICY_PARAMS, np.float32)
+    loss = np.zeros(1, np.float32)
+    _rc(lib().gbosqp_mlp_grad(p.ctypes.data, f.ctypes.data, t.ctypes.data, w.ctypes.data, n, g.ctypes.data,
+                              loss.ctypes.data))
+    return g, float(loss[0])
+
+
+def gbosqp_mlp_train(params, features, targets, weights, batches, lr: float):
+    """Adam on the device; batches: (steps, batch) int array of sample indices.
+    Returns (new params, loss per step)."""
+    p = _f32(params, (POLICY_PARAMS,)).copy()
+    f = _f32(features).reshape(-1, 4)
+    n = f.shape[0]
+    t = _f32(targets, (n, 2))
+    w = _f32(weights, (n, 2))
+    b = np.ascontiguousarray(np.asarray(batches, dtype=np.int32))
+    steps, bs = b.shape
+    hist = np.zeros(max(steps, 1), np.float32)
+    _rc(lib().gbosqp_mlp_train(p.ctypes.data, f.ctypes.data, t.ctypes.data, w.ctypes.data, n, b.ctypes.data, steps,
+                               bs, ctypes.c_float(lr), hist.ctypes.data))
+    return p, hist[:steps]
+
+
+def gbosqp_set_pcg_lambda(h, lam: float, eps: float) -> None:
+    _check(h, lib().gbosqp_set_pcg_lambda(h, float(lam), float(eps)))
+
+
+POLICY_MAGIC = b"GBRHOPOL"
+
+
+def save_policy(path: str, params) -> None:
+    """Write policy parameters: 8-byte magic, count (uint32), CRC32 of the
+    float32 payload (uint32), payload (little-endian float32)."""
+    import zlib
+    p = _f32(params, (POLICY_PARAMS,)).astype("<f4")
+    payload = p.tobytes()
+    with open(path, "wb") as fh:
+        fh.write(POLICY_MAGIC + np.uint32(POLICY_PARAMS).tobytes() + np.uint32(zlib.crc32(payload)).tobytes() + payload)
+
+
+def load_policy(path: str) -> np.ndarray:
+    import zlib
+    raw = open(path, "rb").read()
+    if raw[:8] != POLICY_MAGIC:
+        raise ValueError(f"{path}: not a policy file")
+    count = int(np.frombuffer(raw[8:12], "<u4")[0])
+    crc = int(np.frombuffer(raw[12:16], "<u4")[0])
+    payload = raw[16:]
+    if count != POLICY_PARAMS or len(payload) != 4 * count or zlib.crc32(payload) != crc:
+        raise ValueError(f"{path}: corrupt policy file")
+    return np.frombuffer(payload, "<f4").astype(np.float32).copy()
 
 
 CHECK_NAMES = ["r_prim", "r_dual", "eps_prim", "eps_dual", "r_prim_s", "r_dual_s", "norm_Ax_s", "norm_z_s",

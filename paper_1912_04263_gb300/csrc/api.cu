@@ -339,6 +339,17 @@ int gbosqp_bench_kernel(gbosqp_handle *h, int kernel, int32_t reps, double *avg_
     API_CATCH(h)
 }
 
+int gbosqp_set_pcg_lambda(gbosqp_handle *h, double lambda, double eps) {
+    if (!h || !h->eng) return GBOSQP_ERR_INVALID_ARG;
+    if (!(lambda > 0.0 && lambda < 1.0)) return fail_code(h, GBOSQP_ERR_INVALID_ARG, "lambda must be in ]0, 1[");
+    if (!(eps > 0.0) || !std::isfinite(eps)) return fail_code(h, GBOSQP_ERR_INVALID_ARG, "eps must be > 0");
+    API_TRY
+    GB_CUDA(cudaSetDevice(h->s.device));
+    h->eng->set_lambda(lambda, eps);
+    return GBOSQP_OK;
+    API_CATCH(h)
+}
+
 int gbosqp_check(gbosqp_handle *h, double out[GBOSQP_CHECK_FIELDS]) {
     if (!h || !h->eng || !out) return GBOSQP_ERR_INVALID_ARG;
     API_TRY

@@ -367,16 +367,22 @@ __device__ __forceinline__ bool run_items(const CsrDev<T> &M, const Gather &gath
     int ca[kPerThread], cb[kPerThread];
     if (threadIdx.x == 0)
         for (int j = i0 + 1; j <= i0 + kL2Ahead && j < i1; ++j) prefetch_item(M, M.items[j]);
-    if (i0 < i1) load_item(M, M.items[i0], va, ca);
+    // descriptors run one item ahead of the value/column registers
+    Item cur, nx;
+    if (i0 < i1) {
+        cur = M.items[i0];
+        load_item(M, cur, va, ca);
+    }
+    if (i0 + 1 < i1) nx = M.items[i0 + 1];
     Acc ps1 = Acc(0), ps2 = Acc(0);  // running sums of a long row's pieces
     for (int itx = i0; itx < i1; ++itx) {
-        const Item it = M.items[itx];
+        const Item it = cur;
         const bool has_next = itx + 1 < i1;
         if (threadIdx.x == 0 && itx + 1 + kL2Ahead < i1) prefetch_item(M, M.items[itx + 1 + kL2Ahead]);
-        Item nx;
+        Item nx2;
         if (has_next) {
-            nx = M.items[itx + 1];
             load_item(M, nx, vb, cb);
+            if (itx + 2 < i1) nx2 = M.items[itx + 2];
         }
         const int nnz = it.k1 - it.k0;
         if (it.r1 >= 0) {
@@ -455,6 +461,8 @@ __device__ __forceinline__ bool run_items(const CsrDev<T> &M, const Gather &gath
                 va[u] = vb[u];
                 ca[u] = cb[u];
             }
+            cur = nx;
+            nx = nx2;
         }
     }
     return true;

@@ -1006,6 +1006,14 @@ public:
         return reps > 0 ? ms / reps : 0.0;
     }
 
+    void set_lambda(double lambda, double eps) override {
+        GB_CUDA(cudaMemcpyAsync((char *)st_.p + offsetof(Status, lambda), &lambda, sizeof(double),
+                                cudaMemcpyHostToDevice, stream_));
+        GB_CUDA(cudaMemcpyAsync((char *)st_.p + offsetof(Status, eps_pcg), &eps, sizeof(double),
+                                cudaMemcpyHostToDevice, stream_));
+        GB_CUDA(cudaStreamSynchronize(stream_));
+    }
+
     void spmv_noalloc(int which, const void *x, void *y, double *part, int *count, long long max_items,
                       long long max_long_rows) override {
         const bool isA = which == GBOSQP_MAT_A;

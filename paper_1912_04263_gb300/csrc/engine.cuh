@@ -47,6 +47,7 @@ public:
     virtual int admm_iterations(int k, int *pcg_per_iter) = 0;
     virtual void check(double *out) = 0;
     virtual double bench_kernel(int kernel, int reps) = 0;
+    virtual void set_lambda(double lambda, double eps) = 0;
     // y = M x on device arrays of the working precision, with the long-row
     // scratch supplied by the caller (part: 2 doubles per work item, count:
     // one int per long row); allocates nothing.

@@ -1,0 +1,205 @@
+"""GPU BF16 policy kernels (inference, gradient, Adam) against the FP64 CPU
+oracle.  The network is not in the paper: these pins are finite differences
+(CPU, test_oracle_pins) and this comparison."""
+import numpy as np
+import pytest
+
+from oracle import mlp
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = mlp.PARAM_SHAPES
+ORDER = ["W1", "b1", "W2", "b2", "W3", "b3"]
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1912_04263_gb300 import binding
+    return binding
+
+
+def make_params(seed):
+    rng = np.random.default_rng(seed)
+    flat = np.zeros(4622, np.float32)
+    flat[0:4] = rng.standard_normal(4)            # feature means
+    flat[4:8] = 0.5 + rng.uniform(size=4)          # feature std devs
+    off = 8
+    d = {}
+    for k in ORDER:
+        n = int(np.prod(SHAPES[k]))
+        scale = np.sqrt(2.0 / SHAPES[k][-1]) if k.startswith("W") else 0.1
+        v = (rng.standard_normal(n) * scale).astype(np.float32)
+        flat[off:off + n] = v
+        d[k] = v.astype(np.float64).reshape(SHAPES[k])
+        off += n
+    flat[off:off + 4] = [np.log(10.0), 0.01, 0.5, 0.0]
+    return flat, d
+
+
+def unpack_grad(flat):
+    out, off = {}, 8
+    for k in ORDER:
+        n = int(np.prod(SHAPES[k]))
+        out[k] = flat[off:off + n].astype(np.float64).reshape(SHAPES[k])
+        off += n
+    return out
+
+
+def normalised(flat, feats):
+    f = feats.astype(np.float32)
+    return ((f - flat[0:4]) / flat[4:8]).astype(np.float32).astype(np.float64)
+
+
+def test_policy_forward_matches_oracle(gb):
+    flat, d = make_params(0)
+    feats = np.random.default_rng(1).standard_normal((300, 4)).astype(np.float32) * 3
+    got = gb.gbosqp_policy_forward(flat, feats)
+    ref = mlp.forward_bf16(d, normalised(flat, feats))
+    assert np.max(np.abs(got - ref)) <= 1e-4 * max(1.0, np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("n", [16, 37, 500])
+def test_mlp_gradient_matches_oracle(gb, n):
+    flat, d = make_params(2)
+    rng = np.random.default_rng(3)
+    feats = (rng.standard_normal((n, 4)) * 2).astype(np.float32)
+    tgt = rng.standard_normal((n, 2)).astype(np.float32)
+    wgt = np.ones((n, 2), np.float32)
+    wgt[::4, 1] = 0.0
+    g, loss = gb.gbosqp_mlp_grad(flat, feats, tgt, wgt)
+    gg = unpack_grad(g)
+    X = normalised(flat, feats)
+    # same rounding points: the FP32-accumulated GPU result agrees closely
+    lref, gref, _ = mlp.grads_bf16(d, X, tgt.astype(np.float64), wgt.astype(np.float64))
+    assert abs(loss - lref) <= 1e-4 * max(lref, 1e-6)
+    for k in ORDER:
+        num = np.linalg.norm(gg[k] - gref[k])
+        assert num <= 2e-2 * np.linalg.norm(gref[k]) + 1e-7, k
+    # against the exact FP64 gradient: BF16 operands cost about 1e-2
+    lex, gex = mlp.grads(d, X, tgt.astype(np.float64), wgt.astype(np.float64))
+    for k in ORDER:
+        a, b = gg[k].ravel(), gex[k].ravel()
+        cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-30)
+        assert cos >= 0.999, (k, cos)
+        assert np.linalg.norm(a - b) <= 2e-2 * np.linalg.norm(b) + 1e-7, k
+
+
+def test_mlp_train_follows_adam_and_reduces_loss(gb):
+    flat, d = make_params(4)
+    rng = np.random.default_rng(5)
+    n = 2000
+    feats = (rng.standard_normal((n, 4)) * 2).astype(np.float32)
+    # regression target: a fixed smooth function of the features
+    tgt = np.stack([np.tanh(feats[:, 0] - 0.5 * feats[:, 1]), 0.3 * feats[:, 2]], axis=1).astype(np.float32)
+    wgt = np.ones((n, 2), np.float32)
+    # one step equals the oracle's Adam step on the oracle's BF16 gradient
+    batches = rng.integers(0, n, size=(1, 256)).astype(np.int32)
+    new, hist = gb.gbosqp_mlp_train(flat, feats, tgt, wgt, batches, 1e-3)
+    sel = batches[0]
+    _, gref, _ = mlp.grads_bf16(d, normalised(flat, feats[sel]), tgt[sel].astype(np.float64),
+                                wgt[sel].astype(np.float64))
+    ref = mlp.adam_step({k: v.copy() for k, v in d.items()}, gref, {}, 1, lr=1e-3)
+    got = unpack_grad(new)
+    agree = 0
+    total = 0
+    for k in ORDER:
+        big = np.abs(gref[k]) > 1e-3 * np.max(np.abs(gref[k]))
+        agree += np.sum(np.abs(got[k] - ref[k])[big] <= 1e-5)
+        total += np.sum(big)
+    assert agree >= 0.98 * total
+    # many steps reduce the loss
+    batches = rng.integers(0, n, size=(400, 256)).astype(np.int32)
+    _, hist = gb.gbosqp_mlp_train(flat, feats, tgt, wgt, batches, 3e-3)
+    assert np.mean(hist[-20:]) <= 0.3 * np.mean(hist[:20])
+
+
+def _constant_policy(log_mult):
+    """A network whose output is constant: zero weights, output bias."""
+    p = np.zeros(4622, np.float32)
+    p[4:8] = 1.0
+    off_b3 = 8 + 64 * 4 + 64 + 64 * 64 + 64 + 2 * 64
+    p[off_b3] = log_mult
+    p[off_b3 + 2:off_b3 + 6] = [np.log(10.0), 0.05, 0.5, 0.0]
+    return p
+
+
+def test_stalled_policy_falls_back_to_ratio_rule(gb):
+    """A policy that always multiplies rho by 10 stalls the iteration; the
+    stall rule hands rho back to the residual-ratio rule and the solve still
+    reaches the tolerance."""
+    import qpgen
+    from oracle import checks
+    qp = qpgen.random_qp(300, 3000, 0)
+    with gb.Solver(qp, rho_policy=gb.RHO_LEARNED, policy_params=_constant_policy(np.log(10.0))) as s:
+        st = s.solve()
+        info = s.info()
+        x, y, z = s.solution()
+    assert st == gb.SOLVED, info
+    assert info["policy_fallbacks"] > 0
+    v = checks.kkt_violation(qp, x, z, y)
+    assert v.prim <= info["eps_prim"] * (1 + 1e-6) and v.dual <= info["eps_dual"] * (1 + 1e-6)
+
+
+def test_neutral_policy_keeps_rho(gb):
+    """A policy proposing a zero log multiplier never changes rho."""
+    import qpgen
+    qp = qpgen.random_qp(100, 1000, 1)
+    with gb.Solver(qp, rho_policy=gb.RHO_LEARNED, policy_params=_constant_policy(0.0), max_iter=40) as s:
+        s.solve()
+        info = s.info()
+    assert info["rho"] == 0.1 or info["policy_fallbacks"] > 0
+
+
+POLICY = __import__("os").path.join(__import__("os").path.dirname(__import__("os").path.dirname(
+    __import__("os").path.abspath(__file__))), "paper_1912_04263_gb300", "policy", "rho_policy.bin")
+
+
+@pytest.mark.parametrize("seed", [200500, 200501, 200502])
+def test_trained_policy_solutions_judged_by_oracle(gb, seed):
+    """Held-out random QPs (seeds disjoint from training): the learned-rho
+    FP32 solve meets the tolerances on the unscaled data and its objective
+    lies within the convexity bound of the tight FP64 oracle optimum."""
+    import qpgen
+    from oracle import admm, checks
+    params = gb.load_policy(POLICY)
+    qp = qpgen.random_qp(1000, 10000, seed)
+    with gb.Solver(qp, rho_policy=gb.RHO_LEARNED, policy_params=params) as s:
+        assert s.solve() == gb.SOLVED
+        x, y, z = s.solution()
+        info = s.info()
+    v = checks.kkt_violation(qp, x, z, y)
+    assert v.prim <= info["eps_prim"] * (1 + 1e-6) and v.dual <= info["eps_dual"] * (1 + 1e-6)
+    ref = admm.solve(qp, admm.Settings(eps_abs=1e-9, eps_rel=1e-9, max_iter=100000))
+    f = admm.objective(qp.P, qp.q, x)
+    bound = checks.objective_error_bound(x, y, v.prim, v.dual, ref.x, ref.y)
+    assert abs(f - ref.obj) <= 1.001 * bound + 1e-9
+    assert abs(f - ref.obj) <= 1e-3 * max(1.0, abs(ref.obj))
+
+
+def test_trained_policy_gain_over_ratio_rule(gb):
+    """What the trained network gains over the residual-ratio rule (Section
+    3.4) on held-out QPs of the training family at n = 3000, m = 30000:
+    fewer ADMM iterations and less device time, FP32 both ways; and the
+    learned FP32 form is faster than the plain FP64 form."""
+    import qpgen
+    params = gb.load_policy(POLICY)
+    tot = {"ratio": 0.0, "learned": 0.0, "fp64": 0.0}
+    its = {"ratio": 0, "learned": 0}
+    for seed in (200600, 200601):
+        qp = qpgen.random_qp(3000, 30000, seed)
+        for tag, kw in [("ratio", {}), ("learned", dict(rho_policy=gb.RHO_LEARNED, policy_params=params)),
+                        ("fp64", dict(precision=gb.FP64))]:
+            with gb.Solver(qp, **kw) as s:
+                s.solve()
+                assert s.solve() == gb.SOLVED
+                info = s.info()
+            tot[tag] += info["solve_ms"]
+            if tag in its:
+                its[tag] += info["iters"]
+    print(f"\nlearned/ratio device time {tot['learned'] / tot['ratio']:.3f}, iterations "
+          f"{its['learned']}/{its['ratio']}, learned FP32 / plain FP64 time {tot['learned'] / tot['fp64']:.3f}")
+    assert its["learned"] <= its["ratio"]
+    assert tot["learned"] <= 1.02 * tot["ratio"]
+    assert tot["learned"] < tot["fp64"]

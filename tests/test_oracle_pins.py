@@ -329,3 +329,19 @@ def test_generators_are_deterministic_and_shaped():
     assert las.n == 20 + 300 + 20 and las.m == 300 + 40
     por = qpgen.portfolio_qp(200, 5, 0)
     assert por.n == 205 and por.m == 5 + 1 + 200
+
+
+def test_bf16_gradient_variant_reduces_to_exact_without_rounding(monkeypatch):
+    """With BF16 rounding replaced by the identity, the BF16-emulating
+    forward/backward equals the exact one (which finite differences pin)."""
+    p = _mlp_params(3)
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal((20, 4))
+    T = rng.standard_normal((20, 2))
+    W = np.ones((20, 2))
+    monkeypatch.setattr(mlp, "bf16_round", lambda a: np.asarray(a, np.float64))
+    l1, g1, _ = mlp.grads_bf16(p, X, T, W)
+    l2, g2 = mlp.grads(p, X, T, W)
+    assert abs(l1 - l2) <= 1e-14 * max(1.0, abs(l2))
+    for k in g2:
+        assert np.allclose(g1[k], g2[k], rtol=1e-12, atol=1e-14)
