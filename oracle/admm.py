@@ -29,6 +29,17 @@ the design notes):
   S6  cold start x = z = y = 0, rho_0 = 0.1.
   S7  PCG step length alpha = r'y / p'Kp (Algorithm 3 prints a minus sign
       that contradicts Section 4.1.1 and the cited Nocedal & Wright).
+  S17 infeasibility tests (Section 3.1, approximate forms of eqs.
+      (prim_infeas) and (dual_infeas)) run at every termination check that
+      does not find convergence, on dx = x^k - x^(k-1), dy = y^k - y^(k-1)
+      (unscaled).  Each candidate is scaled to unit inf-norm first: the
+      printed absolute form holds for every converging sequence, whose
+      differences go to zero.  The strict inequalities of the certificates
+      are tested with the margin on the safe side (< -eps, not < eps), so a
+      solvable problem whose iterates drift along a null direction is not
+      reported infeasible.  dy is projected first onto the cone on which
+      the support function of [l, u] is finite (a component that faces an
+      infinite bound is clipped to zero).  eps_pinf = eps_dinf = 1e-4.
 """
 from __future__ import annotations
 
@@ -63,6 +74,8 @@ class Settings:
     pcg_lambda: float = 0.15     # Section 5.3.4
     pcg_eps_min: float = 1e-7    # Section 5.3.4
     max_cg_iter: int = 50
+    eps_prim_inf: float = 1e-4   # S17
+    eps_dual_inf: float = 1e-4   # S17
 
 
 def norm_inf(v) -> float:
@@ -215,6 +228,86 @@ def objective(P, q, x) -> float:
 
 
 # --------------------------------------------------------------------------
+# Infeasibility detection, Section 3.1 (reading S17)
+# --------------------------------------------------------------------------
+
+INF_BOUND = 1e20  # a bound with |v| >= 1e20 is infinite
+
+
+def primal_infeasibility(A, l, u, dy, eps):
+    """Approximate certificate test of eq. (prim_infeas) on dy.
+
+    dy is clipped to the cone where the support function
+    u'(y)_+ + l'(y)_- of the box [l, u] is finite (y_i <= 0 where u_i is
+    infinite, y_i >= 0 where l_i is infinite), scaled to unit inf-norm, and
+    accepted when ||A'y||_inf <= eps and u'(y)_+ + l'(y)_- < -eps.
+    Returns the scaled certificate, or None."""
+    l = np.asarray(l, np.float64)
+    u = np.asarray(u, np.float64)
+    y = np.array(dy, np.float64, copy=True)
+    u_inf = u >= INF_BOUND
+    l_inf = l <= -INF_BOUND
+    y[u_inf] = np.minimum(y[u_inf], 0.0)
+    y[l_inf] = np.maximum(y[l_inf], 0.0)
+    nrm = norm_inf(y)
+    if not (nrm > 0.0 and math.isfinite(nrm)):
+        return None
+    y /= nrm
+    pos, neg = y > 0.0, y < 0.0
+    support = float(u[pos] @ y[pos] + l[neg] @ y[neg])
+    if support < -eps and norm_inf(A.T @ y) <= eps:
+        return y
+    return None
+
+
+def dual_infeasibility(P, q, A, l, u, dx, eps):
+    """Approximate certificate test of eq. (dual_infeas) on dx.
+
+    dx is scaled to unit inf-norm and accepted when ||P x||_inf <= eps,
+    q'x < -eps, and (A x)_i <= eps on rows with a finite upper bound and
+    (A x)_i >= -eps on rows with a finite lower bound.  Returns the scaled
+    certificate, or None."""
+    x = np.array(dx, np.float64, copy=True)
+    nrm = norm_inf(x)
+    if not (nrm > 0.0 and math.isfinite(nrm)):
+        return None
+    x /= nrm
+    if not float(q @ x) < -eps:
+        return None
+    if norm_inf(P @ x) > eps:
+        return None
+    Ax = A @ x
+    l = np.asarray(l, np.float64)
+    u = np.asarray(u, np.float64)
+    if np.any(Ax[u < INF_BOUND] > eps) or np.any(Ax[l > -INF_BOUND] < -eps):
+        return None
+    return x
+
+
+def infeasibility(qp, dx, dy, s: "Settings"):
+    """Primal test first, then dual; returns (status, certificate) or None."""
+    if s.eps_prim_inf > 0.0:
+        y = primal_infeasibility(qp.A, qp.l, qp.u, dy, s.eps_prim_inf)
+        if y is not None:
+            return "primal_infeasible", y
+    if s.eps_dual_inf > 0.0:
+        x = dual_infeasibility(qp.P, qp.q, qp.A, qp.l, qp.u, dx, s.eps_dual_inf)
+        if x is not None:
+            return "dual_infeasible", x
+    return None
+
+
+def _certificate_result(qp, found, k, res, rho, **kw):
+    """Result for an infeasible problem: the certificate in y (primal) or x
+    (dual), NaN elsewhere; objective +inf (primal) or -inf (dual)."""
+    status, cert = found
+    nan_n, nan_m = np.full(qp.n, np.nan), np.full(qp.m, np.nan)
+    if status == "primal_infeasible":
+        return Result(nan_n, nan_m, cert, status, k, math.inf, res, rho, **kw)
+    return Result(cert, nan_m, nan_m, status, k, -math.inf, res, rho, **kw)
+
+
+# --------------------------------------------------------------------------
 # Reduced KKT system and PCG, Section 4 and Section 5.3
 # --------------------------------------------------------------------------
 
@@ -337,6 +430,7 @@ def solve(qp, settings: Settings | None = None, x0=None, y0=None) -> Result:
         sol = F.solve(np.concatenate([s.sigma * x - sc.q, z - y / rv]))
         xt, nu = sol[:n], sol[n:]
         zt = z + (nu - y) / rv
+        x_prev, y_prev = x, y
         x, z, y = admm_update(xt, zt, x, z, y, s.alpha, rv, sc.l, sc.u)
         need_check = (k % s.check_every == 0) or (s.adaptive_rho and k % s.rho_every == 0)
         if need_check:
@@ -345,6 +439,12 @@ def solve(qp, settings: Settings | None = None, x0=None, y0=None) -> Result:
             if k % s.check_every == 0 and res.converged():
                 status = "solved"
                 break
+            if k % s.check_every == 0:
+                xp, _, yp = unscale(sc, x_prev, z, y_prev)
+                found = infeasibility(qp, xu - xp, yu - yp, s)
+                if found is not None:
+                    return _certificate_result(qp, found, k, res, rho, rho_history=hist,
+                                               kkt_rel_residual=max(max_rel, F.max_rel_residual))
             if s.adaptive_rho and k % s.rho_every == 0:
                 res_s = residuals(sc.P, sc.q, sc.A, x, z, y)
                 new_rho = rho_ratio_rule(rho, res_s)
@@ -388,6 +488,7 @@ def solve_pcg(qp, settings: Settings | None = None, max_iter: int | None = None)
         total_cg += out.iters
         per_iter.append(out.iters)
         zt = A @ xt
+        x_prev, y_prev = x, y
         x, z, y = admm_update(xt, zt, x, z, y, s.alpha, rho, sc.l, sc.u)
         if k % s.check_every == 0:
             xu, zu, yu = unscale(sc, x, z, y)
@@ -396,6 +497,11 @@ def solve_pcg(qp, settings: Settings | None = None, max_iter: int | None = None)
             if res.converged():
                 status = "solved"
                 break
+            xp, _, yp = unscale(sc, x_prev, z, y_prev)
+            found = infeasibility(qp, xu - xp, yu - yp, s)
+            if found is not None:
+                return _certificate_result(qp, found, k, res, rho, pcg_iters=total_cg, pcg_per_iter=per_iter,
+                                           rho_history=hist)
             eps = pcg_tolerance(res_s.r_prim, res_s.r_dual, s.pcg_lambda, s.pcg_eps_min)
             if s.adaptive_rho and k % s.rho_every == 0:
                 rho = rho_ratio_rule(rho, res_s)

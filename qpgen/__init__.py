@@ -16,5 +16,7 @@ from .problems import (  # noqa: F401
     rowlen_qp,
     infeasible_primal_qp,
     infeasible_dual_qp,
+    random_primal_infeasible_qp,
+    random_dual_infeasible_qp,
     by_name,
 )

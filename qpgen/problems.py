@@ -241,6 +241,40 @@ def infeasible_dual_qp() -> QP:
               name="infeasible_dual")
 
 
+def random_primal_infeasible_qp(n: int, m: int, seed: int, density: float = 0.3) -> QP:
+    """random_qp(n, m) plus three rows that contradict each other: a1'x >= 1,
+    a2'x >= 1 and (a1 + a2)'x <= 1.5 with a1, a2 N(0,1) dense rows (only the
+    combination y = (-1, -1, 1) of the three rows exposes it)."""
+    base = random_qp(n, m, seed, p_density=density, a_density=density)
+    a = Stream(seed, "pinf/a").normal(2 * n).reshape(2, n)
+    extra = np.vstack([a[0], a[1], a[0] + a[1]])
+    A = _clean(sp.vstack([base.A, sp.csr_matrix(extra)], format="csr"))
+    l = np.concatenate([base.l, [1.0, 1.0, -INF]])
+    u = np.concatenate([base.u, [INF, INF, 1.5]])
+    return QP(base.P, base.q, A, l, u, name=f"pinf_n{n}_m{m}_s{seed}",
+              meta=dict(kind="primal_infeasible", n=n, m=m, seed=seed))
+
+
+def random_dual_infeasible_qp(n: int, m: int, k: int, seed: int, density: float = 0.3) -> QP:
+    """Unbounded QP: variables (x1, x2) with x2 of size k absent from P
+    (P = blkdiag(M M' + 1e-2 I, 0)), q2 < 0 on x2, and x2 entering only
+    rows with an infinite upper bound through nonnegative coefficients; the
+    m rows in x1 alone have l = -U[0,1], u = U[0,1]."""
+    n1 = n - k
+    M = sparse_normal(seed, "dinf/M", n1, n1, density)
+    P1 = M @ M.T + 1e-2 * sp.identity(n1, format="csr")
+    P = _clean(sp.block_diag([P1, sp.csr_matrix((k, k))], format="csr"))
+    A1 = sparse_normal(seed, "dinf/A1", m, n1, density)
+    B1 = sparse_normal(seed, "dinf/B1", k, n1, density)
+    B2 = sp.diags(0.5 + Stream(seed, "dinf/B2").uniform(k))
+    A = _clean(sp.bmat([[A1, None], [B1, B2]], format="csr"))
+    q = np.concatenate([Stream(seed, "dinf/q1").normal(n1), -0.5 - Stream(seed, "dinf/q2").uniform(k)])
+    l = np.concatenate([-Stream(seed, "dinf/l").uniform(m), -1.0 - Stream(seed, "dinf/lb").uniform(k)])
+    u = np.concatenate([Stream(seed, "dinf/u").uniform(m), INF * np.ones(k)])
+    return QP(P, q, A, l, u, name=f"dinf_n{n}_m{m}_k{k}_s{seed}",
+              meta=dict(kind="dual_infeasible", n=n, m=m, k=k, seed=seed))
+
+
 def by_name(name: str, seed: int = 0) -> QP:
     """The named workloads: full-size (C0..C4) and small versions of the same
     families used for oracle-backed parity."""
