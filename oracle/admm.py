@@ -312,25 +312,33 @@ def _certificate_result(qp, found, k, res, rho, **kw):
 # --------------------------------------------------------------------------
 
 def reduced_kkt_apply(P, A, sigma, rho, x):
-    """(P + sigma I + rho A'A) x, evaluated matrix-free as
-    z = rho A x; r = P x + sigma x + A' z (Section 5.3)."""
+    """(P + sigma I + A'RA) x with R = rho I (rho a scalar) or R = diag(rho)
+    (rho a vector, eq. (rho_vec)), evaluated matrix-free as
+    z = R A x; r = P x + sigma x + A' z (Section 5.3)."""
     z = rho * (A @ x)
     return P @ x + sigma * x + A.T @ z
 
 
 def reduced_kkt_rhs(q, A, sigma, rho, x, z, y):
-    """sigma x - q + A'(rho z - y), the right-hand side of eq. (kkt_red_sc)."""
+    """sigma x - q + A'(R z - y), the right-hand side of eq. (kkt_red_sc)
+    (of eq. (kkt_red) for a vector R)."""
     return sigma * x - q + A.T @ (rho * z - y)
 
 
 def jacobi_diag(P, A, sigma, rho):
-    """diag(P) + sigma 1 + rho diag(A'A), with (A'A)_ii = ||A_i||_2^2 the
-    squared norm of column i (Section 5.3.1)."""
+    """diag(P) + sigma 1 + diag(A'RA), with diag(A'RA)_i = rho ||A_:,i||_2^2
+    for R = rho I (Section 5.3.1) and sum_j rho_j A_ji^2 for R = diag(rho)."""
     A = sp.csc_matrix(A)
     colsq = np.zeros(A.shape[1])
+    rv = np.broadcast_to(np.asarray(rho, np.float64), (A.shape[0],))
     for j in range(A.shape[1]):
         seg = A.data[A.indptr[j]:A.indptr[j + 1]]
-        colsq[j] = float(seg @ seg)
+        if np.ndim(rho) == 0:
+            colsq[j] = float(seg @ seg)
+        else:
+            colsq[j] = float((seg * rv[A.indices[A.indptr[j]:A.indptr[j + 1]]]) @ seg)
+    if np.ndim(rho) != 0:
+        return sp.csr_matrix(P).diagonal() + sigma + colsq
     return sp.csr_matrix(P).diagonal() + sigma + rho * colsq
 
 
@@ -473,7 +481,8 @@ def solve_pcg(qp, settings: Settings | None = None, max_iter: int | None = None)
     y = np.zeros(m)
     xt = np.zeros(n)
     rho = s.rho0
-    Minv = 1.0 / jacobi_diag(P, A, s.sigma, rho)
+    rv = rho_vector(rho, sc.l, sc.u, s.rho_vector) if s.rho_vector else rho
+    Minv = 1.0 / jacobi_diag(P, A, s.sigma, rv)
     eps = max(s.pcg_lambda * norm_inf(q), s.pcg_eps_min)
     status = "max_iter"
     total_cg = 0
@@ -482,14 +491,14 @@ def solve_pcg(qp, settings: Settings | None = None, max_iter: int | None = None)
     limit = s.max_iter if max_iter is None else max_iter
     k = 0
     for k in range(1, limit + 1):
-        b = reduced_kkt_rhs(q, A, s.sigma, rho, x, z, y)
-        out = pcg(lambda v: reduced_kkt_apply(P, A, s.sigma, rho, v), b, xt, Minv, eps, s.max_cg_iter)
+        b = reduced_kkt_rhs(q, A, s.sigma, rv, x, z, y)
+        out = pcg(lambda v: reduced_kkt_apply(P, A, s.sigma, rv, v), b, xt, Minv, eps, s.max_cg_iter)
         xt = out.x
         total_cg += out.iters
         per_iter.append(out.iters)
         zt = A @ xt
         x_prev, y_prev = x, y
-        x, z, y = admm_update(xt, zt, x, z, y, s.alpha, rho, sc.l, sc.u)
+        x, z, y = admm_update(xt, zt, x, z, y, s.alpha, rv, sc.l, sc.u)
         if k % s.check_every == 0:
             xu, zu, yu = unscale(sc, x, z, y)
             res = residuals(qp.P, qp.q, qp.A, xu, zu, yu, s.eps_abs, s.eps_rel)
@@ -505,7 +514,8 @@ def solve_pcg(qp, settings: Settings | None = None, max_iter: int | None = None)
             eps = pcg_tolerance(res_s.r_prim, res_s.r_dual, s.pcg_lambda, s.pcg_eps_min)
             if s.adaptive_rho and k % s.rho_every == 0:
                 rho = rho_ratio_rule(rho, res_s)
-                Minv = 1.0 / jacobi_diag(P, A, s.sigma, rho)
+                rv = rho_vector(rho, sc.l, sc.u, s.rho_vector) if s.rho_vector else rho
+                Minv = 1.0 / jacobi_diag(P, A, s.sigma, rv)
                 hist.append(rho)
     xu, zu, yu = unscale(sc, x, z, y)
     res = residuals(qp.P, qp.q, qp.A, xu, zu, yu, s.eps_abs, s.eps_rel)

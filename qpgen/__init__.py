@@ -18,5 +18,8 @@ from .problems import (  # noqa: F401
     infeasible_dual_qp,
     random_primal_infeasible_qp,
     random_dual_infeasible_qp,
+    control_qp,
+    huber_qp,
+    svm_qp,
     by_name,
 )

@@ -17,6 +17,24 @@ measured on:
                s.t. y = F'x,  1'x = 1,  x >= 0.
                F is n x k Bernoulli(density) N(0,1); D = diag(U[0, sqrt(k)]);
                mu ~ N(0,1).
+* control_qp   states x_0..x_T (nx each), inputs u_0..u_{T-1} (nu each):
+               min x_T'Q_T x_T + sum_t x_t'Q x_t + u_t'R u_t
+               s.t. x_0 = x_init, x_{t+1} = A x_t + B u_t, |x_t| <= xbar,
+               |u_t| <= ubar.  A = I + Bernoulli(density) N(0, 0.0025), B
+               Bernoulli(density) N(0,1), Q = diag of Bernoulli(0.7) U[0,10],
+               Q_T = Q, R = 0.1 I, xbar = 1 + U[0,1], ubar = 0.5 + U[0,1],
+               x_init = 0.25 U[-1,1] xbar.
+* huber_qp     Huber fitting of b ~ A x with threshold M = 1 as the QP
+               min u'u + 2M 1'(r + s)  s.t.  A x - u - r + s = b, r, s >= 0
+               (the Huber penalty of a residual a'x - b splits into a
+               quadratic part u and linear parts r, s).  A m x n
+               Bernoulli(density) N(0,1); x_true ~ N(0, 1/n); b = A x_true +
+               e with e ~ N(0, 1/4) and 5% of the entries U[0, 10] outliers.
+* svm_qp       hinge-loss support vector machine, min x'x + lam 1't
+               s.t. t >= diag(b) A x + 1, t >= 0; labels b = +1 on the first
+               half of the m points, -1 on the rest; features Bernoulli(density)
+               with values N(+1/n, 1/n) for b = +1 and N(-1/n, 1/n) for
+               b = -1; lam = 1.
 
 In N(a, b) the second argument is the variance.  P is returned as the full
 symmetric matrix in CSR with sorted column indices; infinite bounds are
@@ -275,6 +293,63 @@ def random_dual_infeasible_qp(n: int, m: int, k: int, seed: int, density: float 
               meta=dict(kind="dual_infeasible", n=n, m=m, k=k, seed=seed))
 
 
+def control_qp(nx: int, nu: int, T: int, seed: int, density: float = 0.3) -> QP:
+    st = lambda tag: Stream(seed, "control/" + tag)  # noqa: E731
+    Ad = sp.identity(nx, format="csr") + sparse_normal(seed, "control/A", nx, nx, density) * 0.05
+    Bd = sparse_normal(seed, "control/B", nx, nu, density)
+    qd = st("Q").uniform(nx) * 10.0
+    qd[st("Qmask").uniform(nx) > 0.7] = 0.0
+    xbar = 1.0 + st("xbar").uniform(nx)
+    ubar = 0.5 + st("ubar").uniform(nu)
+    x0 = 0.25 * (2.0 * st("x0").uniform(nx) - 1.0) * xbar
+    nX, nU = (T + 1) * nx, T * nu
+    # objective: 2 Q on x_0..x_T (Q_T = Q), 2 R on u (the 1/2 x'Px convention)
+    P = _clean(sp.block_diag([sp.diags(np.tile(2.0 * qd, T + 1)), sp.diags(np.full(nU, 0.2))], format="csr"))
+    # dynamics rows: -x_0 = -x_init; A x_t + B u_t - x_{t+1} = 0
+    Ax = sp.kron(sp.eye(T + 1), -sp.eye(nx)) + sp.kron(sp.eye(T + 1, k=-1), Ad)
+    Bu = sp.kron(sp.vstack([sp.csr_matrix((1, T)), sp.eye(T)]), Bd)
+    Aeq = sp.hstack([Ax, Bu])
+    Aineq = sp.identity(nX + nU, format="csr")
+    A = _clean(sp.vstack([Aeq, Aineq], format="csr"))
+    leq = np.concatenate([-x0, np.zeros(T * nx)])
+    lineq = np.concatenate([np.tile(-xbar, T + 1), np.tile(-ubar, T)])
+    uineq = np.concatenate([np.tile(xbar, T + 1), np.tile(ubar, T)])
+    return QP(P, np.zeros(nX + nU), A, np.concatenate([leq, lineq]), np.concatenate([leq, uineq]),
+              name=f"control_nx{nx}_nu{nu}_T{T}_s{seed}",
+              meta=dict(kind="control", nx=nx, nu=nu, T=T, seed=seed, x_init=x0))
+
+
+def huber_qp(n: int, m: int, seed: int, density: float = 0.15, M: float = 1.0) -> QP:
+    Ad = sparse_normal(seed, "huber/A", m, n, density)
+    x_true = Stream(seed, "huber/x").normal(n, 0.0, np.sqrt(1.0 / n))
+    e = Stream(seed, "huber/noise").normal(m, 0.0, 0.5)
+    out = Stream(seed, "huber/outlier").uniform(m) < 0.05
+    e[out] = 10.0 * Stream(seed, "huber/outval").uniform(m)[out]
+    b = Ad @ x_true + e
+    Im = sp.identity(m, format="csr")
+    P = _clean(sp.block_diag([sp.csr_matrix((n, n)), 2.0 * Im, sp.csr_matrix((2 * m, 2 * m))], format="csr"))
+    q = np.concatenate([np.zeros(n + m), 2.0 * M * np.ones(2 * m)])
+    A = _clean(sp.bmat([[Ad, -Im, -Im, Im], [None, None, Im, None], [None, None, None, Im]], format="csr"))
+    l = np.concatenate([b, np.zeros(2 * m)])
+    u = np.concatenate([b, INF * np.ones(2 * m)])
+    return QP(P, q, A, l, u, name=f"huber_n{n}_m{m}_s{seed}", meta=dict(kind="huber", n=n, m=m, seed=seed))
+
+
+def svm_qp(n: int, m: int, seed: int, density: float = 0.15, lam: float = 1.0) -> QP:
+    half = m // 2
+    b = np.concatenate([np.ones(half), -np.ones(m - half)])
+    rows, cols = bernoulli_pattern(Stream(seed, "svm/pattern"), m, n, density)
+    vals = Stream(seed, "svm/values").normal(rows.size, 0.0, np.sqrt(1.0 / n)) + b[rows] / n
+    F = _csr(rows, cols, vals, (m, n))
+    Im = sp.identity(m, format="csr")
+    P = _clean(sp.block_diag([2.0 * sp.identity(n), sp.csr_matrix((m, m))], format="csr"))
+    q = np.concatenate([np.zeros(n), lam * np.ones(m)])
+    A = _clean(sp.bmat([[sp.diags(b) @ F, -Im], [None, Im]], format="csr"))
+    l = np.concatenate([-INF * np.ones(m), np.zeros(m)])
+    u = np.concatenate([-np.ones(m), INF * np.ones(m)])
+    return QP(P, q, A, l, u, name=f"svm_n{n}_m{m}_s{seed}", meta=dict(kind="svm", n=n, m=m, seed=seed))
+
+
 def by_name(name: str, seed: int = 0) -> QP:
     """The named workloads: full-size (C0..C4) and small versions of the same
     families used for oracle-backed parity."""
@@ -291,5 +366,11 @@ def by_name(name: str, seed: int = 0) -> QP:
         "random_300x3000": lambda s: random_qp(300, 3000, s),
         "random_2000x20000": lambda s: random_qp(2000, 20000, s, p_density=5e-3, a_density=0.01),
         "equality_200x100": lambda s: equality_qp(200, 100, s),
+        "control_20x10_T20": lambda s: control_qp(20, 10, 20, s),
+        "huber_50x500": lambda s: huber_qp(50, 500, s),
+        "svm_50x500": lambda s: svm_qp(50, 500, s),
+        # larger members of the same three classes (GPU parity at size)
+        "huber_1000x20000": lambda s: huber_qp(1000, 20000, s),
+        "svm_1000x20000": lambda s: svm_qp(1000, 20000, s),
     }
     return table[name](seed)
