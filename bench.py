@@ -179,8 +179,9 @@ def gpu_arm(args) -> None:
     torch.cuda.synchronize()
 
     policy = None
-    if os.path.exists(POLICY_PATH) and args.policy == "learned":
-        policy = gb.load_policy(POLICY_PATH)
+    policy_file = args.policy_file or POLICY_PATH
+    if os.path.exists(policy_file) and args.policy == "learned":
+        policy = gb.load_policy(policy_file)
 
     def settings(prec):
         s = gb.default_settings(precision=prec, device=local)
@@ -407,6 +408,7 @@ def main():
     ap.add_argument("--lean", action="store_true", help="warm-up steps then one step, minimal output (profiling)")
     ap.add_argument("--policy", default="learned", choices=["learned", "ratio"],
                     help="rho rule of the FP32 form (learned: the committed trained policy, if present)")
+    ap.add_argument("--policy-file", default=None, help="policy weights to use instead of the committed ones")
     ap.add_argument("--loop", default="graph", choices=["graph", "host"],
                     help="host: the same kernels driven by a host loop (profilers cannot attribute kernel "
                          "nodes inside graphs with conditional nodes)")

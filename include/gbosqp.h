@@ -55,8 +55,10 @@ extern "C" {
 #define GBOSQP_SOLVED 1               /* residuals within eq. (termination)  */
 #define GBOSQP_MAX_ITER 2             /* max_iter reached                     */
 #define GBOSQP_NONFINITE 3            /* NaN/inf appeared in the iterates     */
-#define GBOSQP_PRIMAL_INFEASIBLE 4    /* reserved: certificate eq. (prim_infeas) */
-#define GBOSQP_DUAL_INFEASIBLE 5      /* reserved: certificate eq. (dual_infeas) */
+#define GBOSQP_PRIMAL_INFEASIBLE 4    /* approximate certificate of eq. (prim_infeas)
+                                         found (Section 3.1); y holds it       */
+#define GBOSQP_DUAL_INFEASIBLE 5      /* approximate certificate of eq. (dual_infeas)
+                                         found (Section 3.1); x holds it       */
 
 /* ---- enumerations ------------------------------------------------------ */
 #define GBOSQP_FP32 0                 /* matrices and vectors in FP32, PCG dot
@@ -107,6 +109,11 @@ typedef struct {
     double pcg_eps_min;  /* > 0                              default 1e-7 */
     double rho_min;      /* clamp of adapted rho             default 1e-6 */
     double rho_max;      /*                                  default 1e6  */
+    double eps_prim_inf; /* primal infeasibility tolerance, >= 0; 0 turns the
+                            test off (Section 3.1)           default 1e-4 */
+    double eps_dual_inf; /* dual infeasibility tolerance, >= 0; 0 turns the
+                            test off; both 0: the detection kernels are not
+                            part of the solve                default 1e-4 */
     int32_t max_iter;    /* ADMM iterations (rounded up to a multiple of
                             check_every)                     default 4000 */
     int32_t max_cg_iter; /* PCG steps per ADMM iteration     default 50   */
@@ -121,7 +128,17 @@ typedef struct {
     int32_t input_location; /* GBOSQP_HOST | GBOSQP_DEVICE   default HOST */
     int32_t loop_mode;   /* GBOSQP_LOOP_*                    default GRAPH */
     int32_t device;      /* CUDA device ordinal              default 0    */
-    int32_t reserved0;
+    int32_t warm_start;  /* 1: every osqp_solve starts from the iterates
+                            (and rho) the previous solve ended with, as
+                            after a parametric update; 0: cold start unless
+                            osqp_warm_start was called        default 0    */
+    int32_t rho_vector;  /* 0: R = rho I, the paper's choice for the GPU
+                            (Section 5.3); 1: R = rho diag(rs) with
+                            rs_i = 1e3 on rows with l_i = u_i and 1 elsewhere,
+                            OSQP's eq. (rho_vec) (fewer ADMM iterations on
+                            equality-heavy problems, slower PCG)
+                                                             default 0    */
+    int32_t reserved1;
     void *cuda_stream;   /* cudaStream_t to run on; NULL: the library
                             creates and owns one             default NULL */
     const float *policy_params; /* learned policy parameters (host, FP32,
@@ -175,9 +192,15 @@ int osqp_setup(gbosqp_handle **out, const gbosqp_csr *P, const gbosqp_csr *A, co
                const double *l, const double *u, const gbosqp_settings *settings);
 
 /* Run ADMM from a cold start (x = z = y = 0, rho = rho0) or from the point
- * given by osqp_warm_start, until eq. (termination) holds, max_iter, or
- * non-finite iterates.  Returns the status (> 0) or an error (< 0).  The
- * unscaled solution stays on the device until fetched. */
+ * given by osqp_warm_start, until eq. (termination) holds, an infeasibility
+ * certificate is found (Section 3.1: at every termination check the
+ * differences dx = x^k - x^(k-1), dy = y^k - y^(k-1), scaled to unit
+ * inf-norm, are tested against eqs. (prim_infeas) and (dual_infeas) with
+ * the strict inequalities taken as < -eps), max_iter, or non-finite
+ * iterates.  Returns the status (> 0) or an error (< 0).  The unscaled
+ * solution stays on the device until fetched; for an infeasible problem the
+ * certificate (unit inf-norm) is returned in y (primal) or x (dual), the
+ * other vectors are NaN and the objective is +inf (primal) or -inf (dual). */
 int osqp_solve(gbosqp_handle *h);
 
 /* Set rho (Section 5.3.3): only the Jacobi preconditioner is recomputed;
@@ -188,6 +211,21 @@ int osqp_update_rho(gbosqp_handle *h, double rho);
 /* Make the next osqp_solve start from x (n) and y (m) (unscaled, host);
  * z starts at the projection of Ax onto [l, u].  Either may be NULL (zero). */
 int osqp_warm_start(gbosqp_handle *h, const double *x, const double *y);
+
+/* Replace q by q_new (n doubles, on the host, or on the device when the
+ * handle was set up with input_location = GBOSQP_DEVICE) without a new
+ * set-up: the equilibration of osqp_setup is kept (q_bar = c D q_new) and
+ * the tolerances' ||q|| are recomputed.  Matrices, bounds and iterates are
+ * untouched (no counterpart in the paper: OSQP's update call for problems
+ * solved in sequence, e.g. model predictive control).  A NaN or inf in
+ * q_new returns GBOSQP_ERR_NONFINITE and leaves the problem unchanged. */
+int osqp_update_lin_cost(gbosqp_handle *h, const double *q_new);
+
+/* Replace l and/or u (m doubles each, same memory rule as above; NULL keeps
+ * that side) without a new set-up: l_bar = E l, u_bar = E u with the
+ * set-up's E; |v| >= GBOSQP_INFINITY is infinite.  NaN, l > u, l = +inf or
+ * u = -inf returns GBOSQP_ERR_BOUNDS and leaves the problem unchanged. */
+int osqp_update_bounds(gbosqp_handle *h, const double *l_new, const double *u_new);
 
 /* Copy the unscaled solution of the last solve to host arrays x (n), y (m),
  * z (m); any may be NULL. */
@@ -303,6 +341,8 @@ int gbosqp_set_pcg_lambda(gbosqp_handle *h, double lambda, double eps);
 #define GBOSQP_K_ADMM_UPDATE 4    /* z~ = A x~, projection, dual update (SpMV A)        */
 #define GBOSQP_K_CHECK_A 5        /* ||Ax - z|| etc., FP64 accumulation (SpMV A)        */
 #define GBOSQP_K_CHECK_B 6        /* ||Px + q + A'y|| etc., FP64 (SpMV [P A'])          */
+#define GBOSQP_K_INF_A 7          /* A dx against the bounds, dy clipping (SpMV A)       */
+#define GBOSQP_K_INF_B 8          /* ||P dx||, ||A'dy||, q'dx (SpMV [P A'])              */
 
 /* Time `reps` launches of one solve kernel, in the launch configuration the
  * solve uses, on the handle's current vectors, each after a write of twice

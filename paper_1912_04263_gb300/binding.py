@@ -39,10 +39,12 @@ class Settings(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("sigma", ctypes.c_double), ("rho0", ctypes.c_double),
                 ("eps_abs", ctypes.c_double), ("eps_rel", ctypes.c_double), ("pcg_lambda", ctypes.c_double),
                 ("pcg_eps_min", ctypes.c_double), ("rho_min", ctypes.c_double), ("rho_max", ctypes.c_double),
+                ("eps_prim_inf", ctypes.c_double), ("eps_dual_inf", ctypes.c_double),
                 ("max_iter", ctypes.c_int32), ("max_cg_iter", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("rho_every", ctypes.c_int32), ("scaling_iters", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("rho_policy", ctypes.c_int32), ("P_is_upper", ctypes.c_int32), ("input_location", ctypes.c_int32),
-                ("loop_mode", ctypes.c_int32), ("device", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("loop_mode", ctypes.c_int32), ("device", ctypes.c_int32), ("warm_start", ctypes.c_int32),
+                ("rho_vector", ctypes.c_int32), ("reserved1", ctypes.c_int32),
                 ("cuda_stream", ctypes.c_void_p), ("policy_params", ctypes.c_void_p)]
 
 
@@ -101,6 +103,8 @@ def lib():
         "gbosqp_mlp_grad": (i32, [_P, _P, _P, _P, i32, _P, _P]),
         "gbosqp_mlp_train": (i32, [_P, _P, _P, _P, i32, _P, i32, i32, ctypes.c_float, _P]),
         "gbosqp_set_pcg_lambda": (i32, [_P, dbl, dbl]),
+        "osqp_update_lin_cost": (i32, [_P, _P]),
+        "osqp_update_bounds": (i32, [_P, _P, _P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -216,6 +220,21 @@ def osqp_warm_start(h, x=None, y=None) -> None:
     _check(h, lib().osqp_warm_start(h, _ptr(xv), _ptr(yv)))
 
 
+def osqp_update_lin_cost(h, q) -> None:
+    """Replace q (host array) keeping the set-up's equilibration."""
+    n = dims(h)[0]
+    qv = _vec(q, n)
+    _check(h, lib().osqp_update_lin_cost(h, _ptr(qv)))
+
+
+def osqp_update_bounds(h, l=None, u=None) -> None:
+    """Replace l and/or u (host arrays; None keeps that side)."""
+    m = dims(h)[1]
+    lv = None if l is None else _vec(l, m)
+    uv = None if u is None else _vec(u, m)
+    _check(h, lib().osqp_update_bounds(h, _ptr(lv), _ptr(uv)))
+
+
 def dims(h):
     n, m = ctypes.c_int32(), ctypes.c_int32()
     na, npat = ctypes.c_int64(), ctypes.c_int64()
@@ -302,7 +321,8 @@ def gbosqp_admm_iterations(h, k: int):
     return st, per[:k]
 
 
-K_PCG_DIRECTION, K_PCG_KAPPLY, K_PCG_UPDATE, K_PCG_INIT, K_ADMM_UPDATE, K_CHECK_A, K_CHECK_B = range(7)
+(K_PCG_DIRECTION, K_PCG_KAPPLY, K_PCG_UPDATE, K_PCG_INIT, K_ADMM_UPDATE, K_CHECK_A, K_CHECK_B, K_INF_A,
+ K_INF_B) = range(9)
 
 
 def gbosqp_bench_kernel(h, kernel: int, reps: int) -> float:
@@ -439,6 +459,12 @@ class Solver:
 
     def warm_start(self, x=None, y=None):
         osqp_warm_start(self.h, x, y)
+
+    def update_lin_cost(self, q):
+        osqp_update_lin_cost(self.h, q)
+
+    def update_bounds(self, l=None, u=None):
+        osqp_update_bounds(self.h, l, u)
 
     def close(self):
         if getattr(self, "h", None):

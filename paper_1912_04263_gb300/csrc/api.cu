@@ -35,6 +35,9 @@ std::string check_settings(const gbosqp_settings &s) {
     if (!(s.pcg_lambda > 0.0 && s.pcg_lambda < 1.0)) return "pcg_lambda must be in ]0, 1[";
     if (!(s.pcg_eps_min > 0.0)) return "pcg_eps_min must be > 0";
     if (!(s.rho_min > 0.0) || !(s.rho_max >= s.rho_min)) return "need 0 < rho_min <= rho_max";
+    if (!(s.eps_prim_inf >= 0.0) || !(s.eps_dual_inf >= 0.0) || !std::isfinite(s.eps_prim_inf) ||
+        !std::isfinite(s.eps_dual_inf))
+        return "eps_prim_inf and eps_dual_inf must be finite and >= 0";
     if (s.max_iter < 0 || s.max_cg_iter < 0) return "max_iter and max_cg_iter must be >= 0";
     if (s.check_every < 1 || s.check_every > 16) return "check_every must be in 1..16";
     if (s.rho_every < 0 || (s.rho_every > 0 && s.rho_every % s.check_every != 0))
@@ -42,6 +45,8 @@ std::string check_settings(const gbosqp_settings &s) {
     if (s.scaling_iters < 0 || s.scaling_iters > 100) return "scaling_iters must be in 0..100";
     if (s.precision != GBOSQP_FP32 && s.precision != GBOSQP_FP64) return "precision must be FP32 or FP64";
     if (s.rho_policy < 0 || s.rho_policy > 2) return "unknown rho_policy";
+    if (s.warm_start != 0 && s.warm_start != 1) return "warm_start must be 0 or 1";
+    if (s.rho_vector != 0 && s.rho_vector != 1) return "rho_vector must be 0 or 1";
     if (s.rho_policy == GBOSQP_RHO_LEARNED && !s.policy_params) return "learned rho policy needs policy_params";
     if (s.input_location != GBOSQP_HOST && s.input_location != GBOSQP_DEVICE) return "bad input_location";
     if (s.loop_mode != GBOSQP_LOOP_GRAPH && s.loop_mode != GBOSQP_LOOP_HOST) return "bad loop_mode";
@@ -74,6 +79,8 @@ int gbosqp_default_settings(gbosqp_settings *s) {
     s->pcg_eps_min = 1e-7;
     s->rho_min = 1e-6;
     s->rho_max = 1e6;
+    s->eps_prim_inf = 1e-4;
+    s->eps_dual_inf = 1e-4;
     s->max_iter = 4000;
     s->max_cg_iter = 50;
     s->check_every = 5;
@@ -85,6 +92,8 @@ int gbosqp_default_settings(gbosqp_settings *s) {
     s->input_location = GBOSQP_HOST;
     s->loop_mode = GBOSQP_LOOP_GRAPH;
     s->device = 0;
+    s->warm_start = 0;
+    s->rho_vector = 0;
     s->cuda_stream = nullptr;
     s->policy_params = nullptr;
     return GBOSQP_OK;
@@ -174,6 +183,24 @@ int osqp_warm_start(gbosqp_handle *h, const double *x, const double *y) {
     API_TRY
     GB_CUDA(cudaSetDevice(h->s.device));
     h->eng->warm_start(x, y);
+    return GBOSQP_OK;
+    API_CATCH(h)
+}
+
+int osqp_update_lin_cost(gbosqp_handle *h, const double *q) {
+    if (!h || !h->eng || (!q && h->eng->n > 0)) return GBOSQP_ERR_INVALID_ARG;
+    API_TRY
+    GB_CUDA(cudaSetDevice(h->s.device));
+    h->eng->update_lin_cost(q);
+    return GBOSQP_OK;
+    API_CATCH(h)
+}
+
+int osqp_update_bounds(gbosqp_handle *h, const double *l, const double *u) {
+    if (!h || !h->eng) return GBOSQP_ERR_INVALID_ARG;
+    API_TRY
+    GB_CUDA(cudaSetDevice(h->s.device));
+    h->eng->update_bounds(l, u);
     return GBOSQP_OK;
     API_CATCH(h)
 }

@@ -132,16 +132,36 @@ struct Status {
     int fallbacks, stall_count, stall_left, policy_disabled;
     double last_merit, prev_merit;
     int cg_since_update, device_error;
+    // infeasibility detection (Section 3.1): tolerances, whether the tests
+    // run, and the reductions of the two detection kernels
+    double eps_pinf, eps_dinf;
+    double inf_a[4];  // rows of A: max (A dx)_j [u_j finite], max -(A dx)_j
+                      // [l_j finite] (unscaled), ||E dy_bar||, support of dy_bar
+    double inf_b[4];  // rows of [P A']: ||D^-1 P_bar dx_bar||, ||D^-1 A_bar' dy_bar||,
+                      // q_bar'dx_bar, ||D dx_bar||
+    int inf_on;
+    int keep_warm;  // 1: each solve starts from the previous solve's iterates
     // last-block tickets, one per kernel kind
     unsigned int tickets[16];
 };
 
-enum Ticket { kTkI1 = 0, kTkK2, kTkK3, kTkC1, kTkC2, kTkSetupA, kTkSetupB, kTkSetupC, kTkMisc };
+enum Ticket { kTkI1 = 0, kTkK2, kTkK3, kTkC1, kTkC2, kTkSetupA, kTkSetupB, kTkSetupC, kTkMisc, kTkInfA, kTkInfB };
 
 // ------------------------------------------------------------- reductions
 
 __device__ __forceinline__ double nanmax(double a, double b) {
     return (a != a) ? a : ((b != b) ? b : (a > b ? a : b));
+}
+
+// Maximum of two values that are >= 0 (or NaN with a clear sign bit) on
+// their encodings: for such values the IEEE-754 order is the integer order
+// of the bit patterns, and NaN encodings lie above +inf, so a NaN wins as in
+// nanmax.  Runs on the integer pipe (the FP64 pipe is narrow on this GPU).
+// With one operand >= 0 the result is max(that operand, other) whenever the
+// other is >= 0, and that operand when the other is negative.
+__device__ __forceinline__ double amax(double a, double b) {
+    const long long x = __double_as_longlong(a), y = __double_as_longlong(b);
+    return __longlong_as_double(x > y ? x : y);
 }
 
 template <int NS, int NM>
@@ -173,7 +193,7 @@ __device__ __forceinline__ void block_reduce(Red<NS, NM> &red) {
     for (int i = 0; i < NM; ++i) {
         double v = red.m[i];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v = nanmax(v, __shfl_down_sync(0xffffffffu, v, o));
+        for (int o = 16; o > 0; o >>= 1) v = amax(v, __shfl_down_sync(0xffffffffu, v, o));
         if (lane == 0) sred[warp][NS + i] = v;
     }
     __syncthreads();
@@ -187,7 +207,7 @@ __device__ __forceinline__ void block_reduce(Red<NS, NM> &red) {
 #pragma unroll
         for (int i = 0; i < NM; ++i) {
             double a = 0.0;
-            for (int w = 0; w < kWarps; ++w) a = nanmax(a, sred[w][NS + i]);
+            for (int w = 0; w < kWarps; ++w) a = amax(a, sred[w][NS + i]);
             red.m[i] = a;
         }
     }
@@ -222,7 +242,7 @@ __device__ __forceinline__ void grid_finish(Red<NS, NM> &red, double *partials, 
 #pragma unroll
         for (int i = 0; i < NS; ++i) acc.s[i] += __ldcg(partials + (size_t)b * NR + i);
 #pragma unroll
-        for (int i = 0; i < NM; ++i) acc.m[i] = nanmax(acc.m[i], __ldcg(partials + (size_t)b * NR + NS + i));
+        for (int i = 0; i < NM; ++i) acc.m[i] = amax(acc.m[i], __ldcg(partials + (size_t)b * NR + NS + i));
     }
     block_reduce<NS, NM>(acc);
     if (threadIdx.x == 0) {
@@ -265,37 +285,57 @@ __device__ __forceinline__ double to_acc<double, float>(float v) { return f2d_ex
 
 // Row reduction of one block item with lane groups of G threads.  sprod
 // holds the item's products; epi.row(r, s1, s2, red) consumes each row.
+// With G = 1 every thread sums and finishes its own rows.  With G > 1 the
+// groups leave their row sums in rsum and the rows are then finished one
+// per thread, so that the epilogue (a chain of dependent loads, and in the
+// FP64 checks the expensive arithmetic) runs on all lanes instead of on one
+// lane per group; rows are taken in chunks of kThreads.
 template <int G, bool SPLIT, class Acc, class T, class Epi, class RedT>
 __device__ __forceinline__ void reduce_rows(const CsrDev<T> &M, const Item &it, const T *sprod, Epi &epi,
-                                            RedT &red) {
+                                            RedT &red, Acc (*rsum)[kThreads]) {
     const int lane_g = threadIdx.x & (G - 1);
     const int grp = threadIdx.x / G;
     constexpr int ngrp = kThreads / G;
     const int R = it.r1 - it.r0;
-    for (int base = 0; base < R; base += ngrp) {
-        const int r = it.r0 + base + grp;
-        const bool active = (base + grp) < R;
-        Acc s1 = Acc(0), s2 = Acc(0);
-        if (active) {
-            const int a = __ldg(M.rowptr + r) - it.k0;
-            const int b = __ldg(M.rowptr + r + 1) - it.k0;
-            if (SPLIT) {
-                const int sp = __ldg(M.pend + r) - it.k0;
-                for (int e = a + lane_g; e < b; e += G) {
-                    if (e < sp) s1 += to_acc<Acc>(sprod[e]); else s2 += to_acc<Acc>(sprod[e]);
+    for (int c0 = 0; c0 < R; c0 += (G > 1 ? kThreads : R)) {
+        const int cn = G > 1 ? min(kThreads, R - c0) : R;
+        for (int base = 0; base < cn; base += ngrp) {
+            const int lr = base + grp;
+            const int r = it.r0 + c0 + lr;
+            const bool active = lr < cn;
+            Acc s1 = Acc(0), s2 = Acc(0);
+            if (active) {
+                const int a = __ldg(M.rowptr + r) - it.k0;
+                const int b = __ldg(M.rowptr + r + 1) - it.k0;
+                if (SPLIT) {
+                    const int sp = __ldg(M.pend + r) - it.k0;
+                    for (int e = a + lane_g; e < b; e += G) {
+                        if (e < sp) s1 += to_acc<Acc>(sprod[e]); else s2 += to_acc<Acc>(sprod[e]);
+                    }
+                } else {
+                    for (int e = a + lane_g; e < b; e += G) s1 += to_acc<Acc>(sprod[e]);
                 }
-            } else {
-                for (int e = a + lane_g; e < b; e += G) s1 += to_acc<Acc>(sprod[e]);
+            }
+            if (G > 1) {
+#pragma unroll
+                for (int o = G / 2; o > 0; o >>= 1) {
+                    s1 += __shfl_down_sync(0xffffffffu, s1, o, G);
+                    if (SPLIT) s2 += __shfl_down_sync(0xffffffffu, s2, o, G);
+                }
+                if (active && lane_g == 0) {
+                    rsum[0][lr] = s1;
+                    if (SPLIT) rsum[1][lr] = s2;
+                }
+            } else if (active) {
+                epi.row(r, s1, s2, red);
             }
         }
         if (G > 1) {
-#pragma unroll
-            for (int o = G / 2; o > 0; o >>= 1) {
-                s1 += __shfl_down_sync(0xffffffffu, s1, o, G);
-                if (SPLIT) s2 += __shfl_down_sync(0xffffffffu, s2, o, G);
-            }
+            __syncthreads();
+            if ((int)threadIdx.x < cn)
+                epi.row(it.r0 + c0 + threadIdx.x, rsum[0][threadIdx.x], SPLIT ? rsum[1][threadIdx.x] : Acc(0), red);
+            if (c0 + kThreads < R) __syncthreads();  // rsum is refilled by the next chunk
         }
-        if (active && lane_g == 0) epi.row(r, s1, s2, red);
     }
 }
 
@@ -304,30 +344,6 @@ __device__ __forceinline__ void reduce_rows(const CsrDev<T> &M, const Item &it, 
 template <class T, class Acc>
 constexpr size_t rowblock_smem() {
     return (size_t)kCap * sizeof(T);
-}
-
-// Bulk prefetch of [p, p + bytes) into L2 by the copy engine (sm_90+); p
-// 16-byte aligned and bytes a multiple of 16.
-__device__ __forceinline__ void l2_prefetch(const void *p, unsigned bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
-// Items ahead of the current one whose ranges are prefetched into L2.
-#ifndef GB_L2_AHEAD
-#define GB_L2_AHEAD 3
-#endif
-constexpr int kL2Ahead = GB_L2_AHEAD;
-
-// Prefetch the value and column ranges of an item into L2, rounded out to
-// 16-byte boundaries (the arrays carry 8 elements of padding).
-template <class T>
-__device__ __forceinline__ void prefetch_item(const CsrDev<T> &M, const Item &it) {
-    const int k0a = it.k0 & ~3;
-    const int k1a = (it.k1 + 3) & ~3;
-    if (k1a > k0a) {
-        l2_prefetch(M.val + k0a, (unsigned)((k1a - k0a) * sizeof(T)));
-        l2_prefetch(M.col + k0a, (unsigned)((k1a - k0a) * sizeof(int)));
-    }
 }
 
 // Load the value/column range of an item into registers (streaming loads:
@@ -360,13 +376,12 @@ __device__ __forceinline__ bool run_items(const CsrDev<T> &M, const Gather &gath
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sprod = reinterpret_cast<T *>(smem_raw);
     __shared__ Acc wsum[2][kWarps];
+    __shared__ Acc rsum[SPLIT ? 2 : 1][kThreads];
     const int Q = (M.nitems + (int)gridDim.x - 1) / (int)gridDim.x;
     const int i0 = (int)blockIdx.x * Q;
     const int i1 = min(M.nitems, i0 + Q);
     T va[kPerThread], vb[kPerThread];
     int ca[kPerThread], cb[kPerThread];
-    if (threadIdx.x == 0)
-        for (int j = i0 + 1; j <= i0 + kL2Ahead && j < i1; ++j) prefetch_item(M, M.items[j]);
     // descriptors run one item ahead of the value/column registers
     Item cur, nx;
     if (i0 < i1) {
@@ -378,7 +393,6 @@ __device__ __forceinline__ bool run_items(const CsrDev<T> &M, const Gather &gath
     for (int itx = i0; itx < i1; ++itx) {
         const Item it = cur;
         const bool has_next = itx + 1 < i1;
-        if (threadIdx.x == 0 && itx + 1 + kL2Ahead < i1) prefetch_item(M, M.items[itx + 1 + kL2Ahead]);
         Item nx2;
         if (has_next) {
             load_item(M, nx, vb, cb);
@@ -394,11 +408,11 @@ __device__ __forceinline__ bool run_items(const CsrDev<T> &M, const Gather &gath
             __syncthreads();
             const int R = it.r1 - it.r0;
             const int avg = R > 0 ? nnz / R : 0;
-            if (avg >= 24) reduce_rows<32, SPLIT, Acc>(M, it, sprod, epi, red);
-            else if (avg >= 12) reduce_rows<16, SPLIT, Acc>(M, it, sprod, epi, red);
-            else if (avg >= 6) reduce_rows<8, SPLIT, Acc>(M, it, sprod, epi, red);
-            else if (avg >= 3) reduce_rows<4, SPLIT, Acc>(M, it, sprod, epi, red);
-            else reduce_rows<1, SPLIT, Acc>(M, it, sprod, epi, red);
+            if (avg >= 24) reduce_rows<32, SPLIT, Acc>(M, it, sprod, epi, red, rsum);
+            else if (avg >= 12) reduce_rows<16, SPLIT, Acc>(M, it, sprod, epi, red, rsum);
+            else if (avg >= 6) reduce_rows<8, SPLIT, Acc>(M, it, sprod, epi, red, rsum);
+            else if (avg >= 3) reduce_rows<4, SPLIT, Acc>(M, it, sprod, epi, red, rsum);
+            else reduce_rows<1, SPLIT, Acc>(M, it, sprod, epi, red, rsum);
             __syncthreads();
         } else {
             const int row = it.r0;

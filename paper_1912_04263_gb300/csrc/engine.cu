@@ -11,8 +11,10 @@
 //   xt  = [x~ ; t0]  (n+m)    PCG iterate x~ (the warm start) and
 //                             t0 = rho (A x~ - z) + y for the next PCG init
 //   pt  = [p ; t]    (n+m)    PCG direction p and t = rho A p
+//   dxy = [dx ; dy]  (n+m)    x^k - x^(k-1) and y^k - y^(k-1) (scaled)
 //   z, zt (= A x~), l, u (m); q, minv, diagP, colsq, pc (previous p),
-//   kp (K p), r, yv (= M^{-1} r) (n); D, E (double) for unscaling.
+//   kp (K p), r, yv (= M^{-1} r) (n); D, E and their reciprocals (double)
+//   for unscaling.
 //
 // Kernels of one ADMM iteration (each row-block kernel streams one matrix):
 //   pcg_init   PAt: r = P x~ + sigma (x~ - x) + q + A' t0  (= K x~ - b),
@@ -22,13 +24,17 @@
 //   pcg_kp     PAt: Kp = P p + sigma p + A' t, p'Kp    [K-apply, part 2]
 //   pcg_update n:   x~ += a p, r += a Kp, yv = M^{-1} r, r'yv, ||r||_inf,
 //                   beta, stop test ||r||_inf <= eps  [Alg. 3 loop body]
-//   admm_update A:  z~ = A x~; x, z (projection), y (dual), t0
-//                                                   [Alg. 1 steps 5-7]
+//   admm_update A:  z~ = A x~; x, z (projection), y (dual), t0, and the
+//                   iterate differences dx, dy     [Alg. 1 steps 5-7]
 // every check_every iterations:
 //   check_a    A:   ||A x - z||, ||A x||, ||z|| (FP64 accumulation)
+//   inf_a      A:   A dx against the bounds, dy clipped to the cone of
+//                   finite support, ||dy||, support  [Section 3.1]
+//   inf_b      PAt: ||P dx||, ||A'dy||, q'dx, ||dx|| [Section 3.1]
 //   check_b    PAt: ||P x + q + A'y||, ||P x||, ||A'y||, objective; then
-//              eq. (termination), the PCG tolerance of Section 5.3.4 and
-//              the rho update (Section 3.4 / 5.3.3 or the learned policy)
+//              eq. (termination), the infeasibility tests, the PCG
+//              tolerance of Section 5.3.4 and the rho update (Section 3.4 /
+//              5.3.3 or the learned policy)
 //   rho_apply  n, m: M^{-1} and t0 for a changed rho
 #include <math.h>
 
@@ -51,10 +57,12 @@ namespace {
 
 template <class T>
 struct Vecs {
-    T *xy, *xt, *pt;
+    T *xy, *xt, *pt, *dxy;
     T *z, *zt, *l, *u;
     T *q, *minv, *diagp, *colsq, *pc, *kp, *r, *yv;
-    const double *D, *E;
+    const T *rs;  // R = rho diag(rs), eq. (rho_vec): 1e3 on rows with l = u, else 1;
+                  // nullptr for R = rho I (Section 5.3)
+    const double *D, *E, *Dinv, *Einv;
     double *x_out, *y_out, *z_out;
     int n, m;
 };
@@ -69,6 +77,18 @@ constexpr int kMinBlocks = GB_MIN_BLOCKS;
 template <class T>
 __device__ __forceinline__ T clampv(T v, T lo, T hi) {
     return v < lo ? lo : (v > hi ? hi : v);
+}
+
+// rho_j / rho of row j (1 when R = rho I)
+template <class T>
+__device__ __forceinline__ T rscale(const Vecs<T> &v, int j) {
+    return v.rs ? v.rs[j] : T(1);
+}
+
+// |v| as a double, the conversion of a float done on the integer pipe
+template <class T>
+__device__ __forceinline__ double absd(T v) {
+    return to_acc<double>(v < T(0) ? -v : v);
 }
 
 // ------------------------------------------------------------ gathers
@@ -144,7 +164,7 @@ struct EpiInit {
         v.yv[i] = y;
         v.pc[i] = T(0);
         red.s[0] += (double)r * (double)y;
-        red.m[0] = nanmax(red.m[0], fabs((double)r));
+        red.m[0] = amax(red.m[0], absd(r));
     }
 };
 
@@ -173,8 +193,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : 2) k_p
 template <class T>
 struct EpiDir {
     T *t;
+    const T *rs;
     T rho;
-    __device__ __forceinline__ void row(int j, T s1, T, Red<0, 0> &) { t[j] = rho * s1; }
+    __device__ __forceinline__ void row(int j, T s1, T, Red<0, 0> &) { t[j] = (rs ? rho * rs[j] : rho) * s1; }
 };
 
 template <class T>
@@ -183,7 +204,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : 2) k_p
     const int n = v.n;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         v.pt[i] = -v.yv[i] + beta * v.pc[i];
-    EpiDir<T> epi{v.pt + n, T(st->rho)};
+    EpiDir<T> epi{v.pt + n, v.rs, T(st->rho)};
     Red<0, 0> red;
     run_items<T, false>(A, GatherDir<T>{v.yv, v.pc, beta}, epi, red);
 }
@@ -241,7 +262,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(Vecs<T> v, Status *st, 
         v.yv[i] = y;
         v.pc[i] = p;
         red.s[0] += (double)r * (double)y;
-        red.m[0] = nanmax(red.m[0], (double)fabs(r));
+        red.m[0] = amax(red.m[0], absd(r));
     }
     auto fin = [&](const Red<1, 1> &t) {
         if (threadIdx.x != 0) return;
@@ -270,12 +291,20 @@ struct EpiAdmm {
         const T zt = s1;
         const T zr = alpha * zt + (T(1) - alpha) * v.z[j];
         const T y = v.xy[n + j];
-        const T zn = clampv(zr + y * rho_inv, v.l[j], v.u[j]);
-        const T yn = y + rho * (zr - zn);
+        T rj = rho, rij = rho_inv;
+        if (v.rs) {
+            const T sc = v.rs[j];
+            rj = rho * sc;
+            rij = rho_inv / sc;
+        }
+        const T zn = clampv(zr + y * rij, v.l[j], v.u[j]);
+        const T dy = rj * (zr - zn);
+        const T yn = y + dy;
         v.z[j] = zn;
         v.zt[j] = zt;
         v.xy[n + j] = yn;
-        v.xt[n + j] = rho * (zt - zn) + yn;
+        v.dxy[n + j] = dy;
+        v.xt[n + j] = rj * (zt - zn) + yn;
     }
 };
 
@@ -284,8 +313,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : 2) k_a
     const T alpha = T(st->alpha);
     const T rho = T(st->rho);
     const int n = v.n;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        v.xy[i] = alpha * v.xt[i] + (T(1) - alpha) * v.xy[i];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const T x = v.xy[i];
+        const T xn = alpha * v.xt[i] + (T(1) - alpha) * x;
+        v.xy[i] = xn;
+        v.dxy[i] = xn - x;
+    }
     EpiAdmm<T> epi{v, alpha, rho, T(1.0 / st->rho)};
     Red<0, 0> red;
     run_items<T, false>(A, GatherVec<T, T>{v.xt}, epi, red);
@@ -300,15 +333,16 @@ template <class T>
 struct EpiCheckA {
     Vecs<T> v;
     __device__ __forceinline__ void row(int j, double s1, double, Red<0, 6> &red) {
-        const double z = (double)v.z[j];
-        const double rp = s1 - z;
-        const double e = v.E[j];
-        red.m[0] = nanmax(red.m[0], fabs(rp));
-        red.m[1] = nanmax(red.m[1], fabs(s1));
-        red.m[2] = nanmax(red.m[2], fabs(z));
-        red.m[3] = nanmax(red.m[3], fabs(rp) / e);
-        red.m[4] = nanmax(red.m[4], fabs(s1) / e);
-        red.m[5] = nanmax(red.m[5], fabs(z) / e);
+        const double z = to_acc<double>(v.z[j]);
+        const double rp = fabs(s1 - z);
+        const double ax = fabs(s1), az = fabs(z);
+        const double ei = v.Einv[j];
+        red.m[0] = amax(red.m[0], rp);
+        red.m[1] = amax(red.m[1], ax);
+        red.m[2] = amax(red.m[2], az);
+        red.m[3] = amax(red.m[3], rp * ei);
+        red.m[4] = amax(red.m[4], ax * ei);
+        red.m[5] = amax(red.m[5], az * ei);
     }
 };
 
@@ -325,21 +359,120 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_check_a(Cs
     grid_finish<0, 6>(red, partials, &st->tickets[kTkC1], fin);
 }
 
+// Infeasibility detection (Section 3.1), part A (rows of A), on the
+// differences of the last iteration: (A dx)_j = E_j^{-1} (A_bar dx_bar)_j
+// against the finite bounds; dy_bar clipped to the cone where the support
+// function of [l, u] is finite (a component that faces an infinite bound is
+// set to zero) and written back for part B; ||dy|| (times c) and the
+// support l_bar'(dy_bar)_- + u_bar'(dy_bar)_+ (times c).  Sums in the
+// working precision: the tests compare with a relative 1e-4.
+template <class T>
+struct EpiInfA {
+    Vecs<T> v;
+    __device__ __forceinline__ void row(int j, T s1, T, Red<1, 3> &red) {
+        const int n = v.n;
+        const double ad = to_acc<double>(s1) * v.Einv[j];
+        const T l = v.l[j], u = v.u[j];
+        const bool lfin = l > -T(INFINITY), ufin = u < T(INFINITY);
+        if (ufin) red.m[0] = amax(red.m[0], ad);    // keeps max(0, ...)
+        if (lfin) red.m[1] = amax(red.m[1], -ad);
+        T dy = v.dxy[n + j];
+        if (!ufin && dy > T(0)) dy = T(0);
+        if (!lfin && dy < T(0)) dy = T(0);
+        v.dxy[n + j] = dy;
+        red.m[2] = amax(red.m[2], absd(dy) * v.E[j]);
+        if (dy > T(0)) red.s[0] += to_acc<double>(u) * to_acc<double>(dy);
+        else if (dy < T(0)) red.s[0] += to_acc<double>(l) * to_acc<double>(dy);
+    }
+};
+
+template <class T>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_inf_a(CsrDev<T> A, Vecs<T> v, Status *st, double *partials) {
+    EpiInfA<T> epi{v};
+    Red<1, 3> red;
+    red.zero();
+    run_items<T, false>(A, GatherVec<T, T>{v.dxy}, epi, red);
+    auto fin = [&](const Red<1, 3> &t) {
+        if (threadIdx.x != 0) return;
+        st->inf_a[0] = t.m[0];
+        st->inf_a[1] = t.m[1];
+        st->inf_a[2] = t.m[2];
+        st->inf_a[3] = t.s[0];
+    };
+    grid_finish<1, 3>(red, partials, &st->tickets[kTkInfA], fin);
+}
+
+// Part B (rows of [P A']): ||D^-1 P_bar dx_bar|| and ||D^-1 A_bar' dy_bar||
+// (c times the unscaled ||P dx|| and ||A'dy||), q_bar'dx_bar (c q'dx) and
+// ||D dx_bar|| = ||dx||.
+template <class T>
+struct EpiInfB {
+    Vecs<T> v;
+    __device__ __forceinline__ void row(int i, T pdx, T atdy, Red<1, 3> &red) {
+        const double di = v.Dinv[i];
+        const T dx = v.dxy[i];
+        red.m[0] = amax(red.m[0], absd(pdx) * di);
+        red.m[1] = amax(red.m[1], absd(atdy) * di);
+        red.m[2] = amax(red.m[2], absd(dx) * v.D[i]);
+        red.s[0] += to_acc<double>(v.q[i]) * to_acc<double>(dx);
+    }
+};
+
+template <class T>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_inf_b(CsrDev<T> PAt, Vecs<T> v, Status *st, double *partials) {
+    EpiInfB<T> epi{v};
+    Red<1, 3> red;
+    red.zero();
+    run_items<T, true>(PAt, GatherVec<T, T>{v.dxy}, epi, red);
+    auto fin = [&](const Red<1, 3> &t) {
+        if (threadIdx.x != 0) return;
+        st->inf_b[0] = t.m[0];
+        st->inf_b[1] = t.m[1];
+        st->inf_b[2] = t.s[0];
+        st->inf_b[3] = t.m[2];
+    };
+    grid_finish<1, 3>(red, partials, &st->tickets[kTkInfB], fin);
+}
+
+// The approximate certificate tests of Section 3.1 on the normalised
+// differences (the margins of the strict certificate inequalities on the
+// safe side, -eps): primal when ||A'dy|| <= eps ||dy|| and support < -eps
+// ||dy||; dual when ||P dx|| <= eps ||dx||, q'dx < -eps ||dx|| and A dx
+// within eps ||dx|| of the recession cone of [l, u].  Unscaled, dy = E
+// dy_bar / c, A'dy = D^-1 A_bar' dy_bar / c and the support carry 1/c, which
+// cancels in the primal test; dx = D dx_bar and A dx = E^-1 A_bar dx_bar
+// carry none while P dx = D^-1 P_bar dx_bar / c and q'dx = q_bar'dx_bar / c
+// do, so the dual test applies 1/c to those two.
+__device__ __forceinline__ int infeasibility_status(const Status *st) {
+    if (!st->inf_on) return 0;
+    const double ndy = st->inf_a[2];
+    if (st->eps_pinf > 0.0 && ndy > 0.0 && isfinite(ndy) && st->inf_a[3] < -st->eps_pinf * ndy &&
+        st->inf_b[1] <= st->eps_pinf * ndy)
+        return GBOSQP_PRIMAL_INFEASIBLE;
+    const double ndx = st->inf_b[3];
+    const double tol = st->eps_dinf * ndx;
+    if (st->eps_dinf > 0.0 && ndx > 0.0 && isfinite(ndx) && st->inf_b[2] * st->cinv < -tol &&
+        st->inf_b[0] * st->cinv <= tol && st->inf_a[0] <= tol && st->inf_a[1] <= tol)
+        return GBOSQP_DUAL_INFEASIBLE;
+    return 0;
+}
+
 // Part B (rows of [P A']): r_dual = P x + q + A'y, FP64 sums; objective.
 template <class T>
 struct EpiCheckB {
     Vecs<T> v;
     __device__ __forceinline__ void row(int i, double px, double aty, Red<1, 6> &red) {
-        const double q = (double)v.q[i];
-        const double rd = px + q + aty;
-        const double d = v.D[i];
-        red.m[0] = nanmax(red.m[0], fabs(rd));
-        red.m[1] = nanmax(red.m[1], fabs(px));
-        red.m[2] = nanmax(red.m[2], fabs(aty));
-        red.m[3] = nanmax(red.m[3], fabs(rd) / d);
-        red.m[4] = nanmax(red.m[4], fabs(px) / d);
-        red.m[5] = nanmax(red.m[5], fabs(aty) / d);
-        red.s[0] += (double)v.xy[i] * (0.5 * px + q);
+        const double q = to_acc<double>(v.q[i]);
+        const double rd = fabs(px + q + aty);
+        const double apx = fabs(px), aaty = fabs(aty);
+        const double di = v.Dinv[i];
+        red.m[0] = amax(red.m[0], rd);
+        red.m[1] = amax(red.m[1], apx);
+        red.m[2] = amax(red.m[2], aaty);
+        red.m[3] = amax(red.m[3], rd * di);
+        red.m[4] = amax(red.m[4], apx * di);
+        red.m[5] = amax(red.m[5], aaty * di);
+        red.s[0] += to_acc<double>(v.xy[i]) * (0.5 * px + q);
     }
 };
 
@@ -372,7 +505,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_check_b(Cs
             int status = 0;
             if (!finite || st->device_error) status = GBOSQP_NONFINITE;
             else if (conv) status = GBOSQP_SOLVED;
-            else if (st->k >= st->max_iter) status = GBOSQP_MAX_ITER;
+            else if ((status = infeasibility_status(st)) != 0) {
+                st->obj = status == GBOSQP_PRIMAL_INFEASIBLE ? INFINITY : -INFINITY;
+            } else if (st->k >= st->max_iter) status = GBOSQP_MAX_ITER;
             st->status = status;
             if (status == 0) {
                 st->eps_pcg = fmax(st->lambda * sqrt(st->rp_s * st->rd_s), st->eps_min);
@@ -415,24 +550,31 @@ __global__ void __launch_bounds__(kThreads) k_rho_apply(Vecs<T> v, const Status 
     const long long N = n > m ? n : m;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
         if (i < n) v.minv[i] = T(1.0 / ((double)v.diagp[i] + sigma + rho * (double)v.colsq[i]));
-        if (i < m) v.xt[n + i] = T(rho) * (v.zt[i] - v.z[i]) + v.xy[n + i];
+        if (i < m) v.xt[n + i] = T(rho) * rscale(v, (int)i) * (v.zt[i] - v.z[i]) + v.xy[n + i];
     }
 }
 
-// Unscaled output: x = D x_bar, z = z_bar / E, y = E y_bar / c.
+// Unscaled output: x = D x_bar, z = z_bar / E, y = E y_bar / c.  For an
+// infeasible problem the certificate of unit inf-norm takes the place of y
+// (primal: E dy_bar / ||E dy_bar||) or of x (dual: D dx_bar / ||D dx_bar||)
+// and the other outputs are NaN.
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_output(Vecs<T> v, Status *st) {
     const int n = v.n, m = v.m;
     const double cinv = st->cinv;
+    const int status = st->status;
+    const bool pinf = status == GBOSQP_PRIMAL_INFEASIBLE, dinf = status == GBOSQP_DUAL_INFEASIBLE;
+    const double sy = pinf ? 1.0 / st->inf_a[2] : 0.0, sx = dinf ? 1.0 / st->inf_b[3] : 0.0;
     const long long N = n > m ? n : m;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-        if (i < n) v.x_out[i] = v.D[i] * (double)v.xy[i];
+        if (i < n)
+            v.x_out[i] = pinf ? (double)NAN : (dinf ? v.D[i] * (double)v.dxy[i] * sx : v.D[i] * (double)v.xy[i]);
         if (i < m) {
-            v.z_out[i] = (double)v.z[i] / v.E[i];
-            v.y_out[i] = v.E[i] * (double)v.xy[n + i] * cinv;
+            v.z_out[i] = (pinf || dinf) ? (double)NAN : (double)v.z[i] * v.Einv[i];
+            v.y_out[i] = dinf ? (double)NAN : (pinf ? v.E[i] * (double)v.dxy[n + i] * sy : v.E[i] * (double)v.xy[n + i] * cinv);
         }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) st->warm = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->warm = st->keep_warm;
 }
 
 // Generic y = alpha M x (test hook and set-up helpers).
@@ -461,7 +603,80 @@ __global__ void __launch_bounds__(kThreads) k_spmv_dbl(CsrDev<T> M, const T *x, 
 template <class T>
 __global__ void k_t0(Vecs<T> v, double rho) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < v.m) v.xt[v.n + j] = T(rho) * (v.zt[j] - v.z[j]) + v.xy[v.n + j];
+    if (j < v.m) v.xt[v.n + j] = T(rho) * rscale(v, j) * (v.zt[j] - v.z[j]) + v.xy[v.n + j];
+}
+
+// Parametric updates: q_bar = c D q, and |q_bar|, |q_bar| / D maxima (on
+// the bit patterns of the non-negative values) for the tolerances; a
+// non-finite entry sets flag.
+__global__ void k_scale_q(double *q, const double *D, double c, int n, unsigned long long *norms, int *flag) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double v = q[i];
+    if (!isfinite(v)) atomicOr(flag, 1);
+    const double s = c * D[i] * v;
+    q[i] = s;
+    const double a = fabs(s);
+    atomicMax(norms, (unsigned long long)__double_as_longlong(a));
+    atomicMax(norms + 1, (unsigned long long)__double_as_longlong(a / D[i]));
+}
+
+// l_bar = E l, u_bar = E u with |v| >= 1e20 taken as infinite; a missing
+// side (nullptr) keeps its current scaled value.  NaN, l > u, l = +inf or
+// u = -inf set flag.
+template <class T>
+__global__ void k_scale_bounds(const double *l, const double *u, const double *E, int m, const T *lcur, const T *ucur,
+                               double *lo, double *uo, int *flag) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    double a, b;
+    if (l) {
+        a = l[i];
+        if (a != a) atomicOr(flag, 1);
+        a = a <= -kInf ? -INFINITY : (a >= kInf ? INFINITY : a * E[i]);
+    } else {
+        a = (double)lcur[i];
+    }
+    if (u) {
+        b = u[i];
+        if (b != b) atomicOr(flag, 1);
+        b = b >= kInf ? INFINITY : (b <= -kInf ? -INFINITY : b * E[i]);
+    } else {
+        b = (double)ucur[i];
+    }
+    if (a > b || a == INFINITY || b == -INFINITY) atomicOr(flag, 1);
+    lo[i] = a;
+    uo[i] = b;
+}
+
+// eq. (rho_vec): rs_j = 1e3 where l_j = u_j (scaled bounds), else 1
+template <class T>
+__global__ void k_rho_scale(const T *l, const T *u, int m, T *rs) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < m) rs[j] = l[j] == u[j] ? T(1e3) : T(1);
+}
+
+// colsq_i = sum_j rs_j A_ji^2 over the A' part of row i of [P A'] (one
+// warp per row, FP64 sums): the diagonal of A'RA / rho for the Jacobi
+// preconditioner with a rho vector
+template <class T>
+__global__ void k_colsq_weighted(const int *rowptr, const int *col, const int *pend, const T *val, const T *rs,
+                                 int n, T *colsq) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (w >= n) return;
+    double acc = 0.0;
+    for (int k = pend[w] + lane; k < rowptr[w + 1]; k += 32) {
+        const double a = (double)val[k];
+        acc += a * a * (double)rs[col[k] - n];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) colsq[w] = T(acc);
+}
+
+__global__ void k_recip(const double *in, double *out, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = 1.0 / in[i];
 }
 
 template <class T>
@@ -578,6 +793,7 @@ public:
         // vectors
         const size_t nm = (size_t)n + m;
         xy_.alloc(sizeof(T) * std::max<size_t>(nm, 1));
+        dxy_.alloc(sizeof(T) * std::max<size_t>(nm, 1));
         xt_.alloc(sizeof(T) * std::max<size_t>(nm, 1));
         pt_.alloc(sizeof(T) * std::max<size_t>(nm, 1));
         for (DevBuf *b : {&z_, &zt_}) b->alloc(sizeof(T) * std::max(m, 1));
@@ -592,6 +808,11 @@ public:
         y_out_.alloc(sizeof(double) * std::max(m, 1));
         z_out_.alloc(sizeof(double) * std::max(m, 1));
         GB_CUDA(cudaMemsetAsync(xy_.p, 0, xy_.bytes, stream_));
+        GB_CUDA(cudaMemsetAsync(dxy_.p, 0, dxy_.bytes, stream_));
+        Dinv_.alloc(sizeof(double) * std::max(n, 1));
+        Einv_.alloc(sizeof(double) * std::max(m, 1));
+        if (n) launch(k_recip, ceil_div(n, 256), 256, stream_, D_.as<double>(), Dinv_.as<double>(), (long long)n);
+        if (m) launch(k_recip, ceil_div(m, 256), 256, stream_, E_.as<double>(), Einv_.as<double>(), (long long)m);
         GB_CUDA(cudaMemsetAsync(xt_.p, 0, xt_.bytes, stream_));
         GB_CUDA(cudaMemsetAsync(z_.p, 0, z_.bytes, stream_));
         GB_CUDA(cudaMemsetAsync(zt_.p, 0, zt_.bytes, stream_));
@@ -601,7 +822,8 @@ public:
         // launch geometry and reduction scratch
         // dynamic shared memory of the pipelined row-block kernels
         for (const void *k : {(const void *)k_pcg_p_t<T>, (const void *)k_pcg_kp<T>, (const void *)k_pcg_init<T>,
-                              (const void *)k_admm_update<T>, (const void *)k_spmv<T, T>})
+                              (const void *)k_admm_update<T>, (const void *)k_spmv<T, T>, (const void *)k_inf_a<T>,
+                              (const void *)k_inf_b<T>})
             GB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemT));
         for (const void *k : {(const void *)k_check_a<T>, (const void *)k_check_b<T>, (const void *)k_spmv_dbl<T>})
             GB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemD));
@@ -612,11 +834,13 @@ public:
         gKp_ = grid_for_items(planPAt_.nitems, (const void *)k_pcg_kp<T>, kSmemT);
         gInit_ = grid_for_items(planPAt_.nitems, (const void *)k_pcg_init<T>, kSmemT);
         gCb_ = grid_for_items(planPAt_.nitems, (const void *)k_check_b<T>, kSmemD);
+        gIa_ = grid_for_items(planA_.nitems, (const void *)k_inf_a<T>, kSmemT);
+        gIb_ = grid_for_items(planPAt_.nitems, (const void *)k_inf_b<T>, kSmemT);
         // vector kernels: about 4 elements per thread
         const int cap = device_sm_count() * 8;
         gridVec_ = std::max(1, std::min(grid_for_n(n, kThreads), cap));
         gridN_ = std::max(1, std::min(grid_for_n(std::max(n, m), kThreads * 4), cap));
-        const int maxgrid = std::max({gPt_, gAdmm_, gCa_, gKp_, gInit_, gCb_, gridN_, gridVec_});
+        const int maxgrid = std::max({gPt_, gAdmm_, gCa_, gKp_, gInit_, gCb_, gIa_, gIb_, gridN_, gridVec_});
         partials_.alloc(sizeof(double) * (size_t)maxgrid * 8);
         // status block
         Status h;
@@ -645,6 +869,11 @@ public:
         h.check_every = ce;
         h.rho_every = s.rho_every;
         h.policy = s.rho_policy;
+        h.eps_pinf = s.eps_prim_inf;
+        h.eps_dinf = s.eps_dual_inf;
+        h.inf_on = (s.eps_prim_inf > 0.0 || s.eps_dual_inf > 0.0) ? 1 : 0;
+        h.keep_warm = s.warm_start ? 1 : 0;
+        inf_on_ = h.inf_on != 0;
         st_.alloc(sizeof(Status));
         st2_.alloc(sizeof(Status));
         GB_CUDA(cudaMemcpyAsync(st_.p, &h, sizeof(h), cudaMemcpyHostToDevice, stream_));
@@ -653,6 +882,10 @@ public:
             policy_.alloc(sizeof(float) * GBOSQP_POLICY_PARAMS);
             GB_CUDA(cudaMemcpyAsync(policy_.p, s.policy_params, sizeof(float) * GBOSQP_POLICY_PARAMS,
                                     cudaMemcpyHostToDevice, stream_));
+        }
+        if (s.rho_vector) {
+            rs_.alloc(sizeof(T) * std::max(m, 1));
+            rho_vector_setup();
         }
         GB_CUDA(cudaStreamSynchronize(stream_));
         if (s.loop_mode == GBOSQP_LOOP_GRAPH) build_graph();
@@ -689,9 +922,9 @@ public:
         if (exec_) {
             // kernels executed by the graph: reset, output, per iteration
             // pcg_init and admm_update, per PCG step three kernels, per
-            // check three kernels
+            // check three kernels (five with infeasibility detection)
             const long long checks = s_.check_every > 0 ? h.k / s_.check_every : 0;
-            solve_launches += 2 + 2LL * h.k + 3LL * h.cg_total + 3LL * checks;
+            solve_launches += 2 + 2LL * h.k + 3LL * h.cg_total + (inf_on_ ? 5LL : 3LL) * checks;
         }
         return h.status;
     }
@@ -728,6 +961,56 @@ public:
                                 stream_));
         GB_CUDA(cudaMemcpyAsync((char *)st_.p + offsetof(Status, rho), &h.rho0, sizeof(double), cudaMemcpyHostToDevice,
                                 stream_));
+        GB_CUDA(cudaGetLastError());
+        GB_CUDA(cudaStreamSynchronize(stream_));
+    }
+
+    void update_lin_cost(const double *q) override {
+        DevBuf qd(sizeof(double) * std::max(n, 1)), norms(2 * sizeof(unsigned long long)), flag(sizeof(int));
+        const cudaMemcpyKind kind = s_.input_location == GBOSQP_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        if (n) GB_CUDA(cudaMemcpyAsync(qd.p, q, sizeof(double) * n, kind, stream_));
+        GB_CUDA(cudaMemsetAsync(norms.p, 0, norms.bytes, stream_));
+        GB_CUDA(cudaMemsetAsync(flag.p, 0, flag.bytes, stream_));
+        if (n) launch(k_scale_q, ceil_div(n, 256), 256, stream_, qd.as<double>(), D_.as<double>(), c_, n,
+                      norms.as<unsigned long long>(), flag.as<int>());
+        int bad = 0;
+        double qn[2] = {0.0, 0.0};
+        GB_CUDA(cudaMemcpyAsync(&bad, flag.p, sizeof(int), cudaMemcpyDeviceToHost, stream_));
+        GB_CUDA(cudaMemcpyAsync(qn, norms.p, sizeof(qn), cudaMemcpyDeviceToHost, stream_));
+        GB_CUDA(cudaStreamSynchronize(stream_));
+        if (bad) fail(GBOSQP_ERR_NONFINITE, "q holds a NaN or an infinite value");
+        if (n) launch(k_from_double<T>, ceil_div(n, 256), 256, stream_, qd.as<double>(), q_.as<T>(), (long long)n);
+        const double eps0 = std::max(s_.pcg_lambda * qn[0], s_.pcg_eps_min);
+        GB_CUDA(cudaMemcpyAsync((char *)st_.p + offsetof(Status, qnorm_s), &qn[0], sizeof(double), cudaMemcpyHostToDevice, stream_));
+        GB_CUDA(cudaMemcpyAsync((char *)st_.p + offsetof(Status, qnorm_u), &qn[1], sizeof(double), cudaMemcpyHostToDevice, stream_));
+        GB_CUDA(cudaMemcpyAsync((char *)st_.p + offsetof(Status, eps0), &eps0, sizeof(double), cudaMemcpyHostToDevice, stream_));
+        GB_CUDA(cudaGetLastError());
+        GB_CUDA(cudaStreamSynchronize(stream_));
+    }
+
+    void update_bounds(const double *l, const double *u) override {
+        if (!m || (!l && !u)) return;
+        const cudaMemcpyKind kind = s_.input_location == GBOSQP_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        DevBuf li, ui, lo(sizeof(double) * m), uo(sizeof(double) * m), flag(sizeof(int));
+        if (l) {
+            li.alloc(sizeof(double) * m);
+            GB_CUDA(cudaMemcpyAsync(li.p, l, sizeof(double) * m, kind, stream_));
+        }
+        if (u) {
+            ui.alloc(sizeof(double) * m);
+            GB_CUDA(cudaMemcpyAsync(ui.p, u, sizeof(double) * m, kind, stream_));
+        }
+        GB_CUDA(cudaMemsetAsync(flag.p, 0, flag.bytes, stream_));
+        launch(k_scale_bounds<T>, ceil_div(m, 256), 256, stream_, (const double *)li.as<double>(),
+               (const double *)ui.as<double>(), E_.as<double>(), m, (const T *)l_.as<T>(), (const T *)u_.as<T>(),
+               lo.as<double>(), uo.as<double>(), flag.as<int>());
+        int bad = 0;
+        GB_CUDA(cudaMemcpyAsync(&bad, flag.p, sizeof(int), cudaMemcpyDeviceToHost, stream_));
+        GB_CUDA(cudaStreamSynchronize(stream_));
+        if (bad) fail(GBOSQP_ERR_BOUNDS, "bounds hold a NaN, l > u, l = +inf or u = -inf");
+        launch(k_from_double<T>, ceil_div(m, 256), 256, stream_, lo.as<double>(), l_.as<T>(), (long long)m);
+        launch(k_from_double<T>, ceil_div(m, 256), 256, stream_, uo.as<double>(), u_.as<T>(), (long long)m);
+        if (s_.rho_vector) rho_vector_setup();  // the equality rows may have changed
         GB_CUDA(cudaGetLastError());
         GB_CUDA(cudaStreamSynchronize(stream_));
     }
@@ -944,7 +1227,8 @@ public:
         Vecs<T> v = vecs();
         // the timed kernels read and write the solve's vectors; keep a copy
         // of the state they modify and restore it afterwards
-        DevBuf save_xy(xy_.bytes), save_xt(xt_.bytes), save_z(z_.bytes), save_zt(zt_.bytes);
+        DevBuf save_xy(xy_.bytes), save_xt(xt_.bytes), save_z(z_.bytes), save_zt(zt_.bytes), save_dxy(dxy_.bytes);
+        GB_CUDA(cudaMemcpyAsync(save_dxy.p, dxy_.p, dxy_.bytes, cudaMemcpyDeviceToDevice, stream_));
         GB_CUDA(cudaMemcpyAsync(save_xy.p, xy_.p, xy_.bytes, cudaMemcpyDeviceToDevice, stream_));
         GB_CUDA(cudaMemcpyAsync(save_xt.p, xt_.p, xt_.bytes, cudaMemcpyDeviceToDevice, stream_));
         GB_CUDA(cudaMemcpyAsync(save_z.p, z_.p, z_.bytes, cudaMemcpyDeviceToDevice, stream_));
@@ -958,6 +1242,8 @@ public:
                 case GBOSQP_K_ADMM_UPDATE: launch_smem(k_admm_update<T>, gAdmm_, kThreads, kSmemT, stream_, csrA(), v, st); break;
                 case GBOSQP_K_CHECK_A: launch_smem(k_check_a<T>, gCa_, kThreads, kSmemD, stream_, csrA(), v, st, partials_.as<double>()); break;
                 case GBOSQP_K_CHECK_B: launch_smem(k_check_b<T>, gCb_, kThreads, kSmemD, stream_, csrPAt(), v, st, partials_.as<double>(), policy(), (cudaGraphConditionalHandle)0, 0); break;
+                case GBOSQP_K_INF_A: launch_smem(k_inf_a<T>, gIa_, kThreads, kSmemT, stream_, csrA(), v, st, partials_.as<double>()); break;
+                case GBOSQP_K_INF_B: launch_smem(k_inf_b<T>, gIb_, kThreads, kSmemT, stream_, csrPAt(), v, st, partials_.as<double>()); break;
                 default: fail(GBOSQP_ERR_INVALID_ARG, "unknown kernel selector");
             }
         };
@@ -999,6 +1285,7 @@ public:
         };
         const float ms = std::max(0.f, time_graph(true) - time_graph(false));
         GB_CUDA(cudaMemcpyAsync(xy_.p, save_xy.p, xy_.bytes, cudaMemcpyDeviceToDevice, stream_));
+        GB_CUDA(cudaMemcpyAsync(dxy_.p, save_dxy.p, dxy_.bytes, cudaMemcpyDeviceToDevice, stream_));
         GB_CUDA(cudaMemcpyAsync(xt_.p, save_xt.p, xt_.bytes, cudaMemcpyDeviceToDevice, stream_));
         GB_CUDA(cudaMemcpyAsync(z_.p, save_z.p, z_.bytes, cudaMemcpyDeviceToDevice, stream_));
         GB_CUDA(cudaMemcpyAsync(zt_.p, save_zt.p, zt_.bytes, cudaMemcpyDeviceToDevice, stream_));
@@ -1083,12 +1370,23 @@ private:
         M.err = &(st_.template as<Status>()->device_error);
         return M;
     }
+    // rs from the scaled bounds, and the weighted column sums it implies
+    void rho_vector_setup() {
+        if (m) launch(k_rho_scale<T>, ceil_div(m, 256), 256, stream_, (const T *)l_.as<T>(), (const T *)u_.as<T>(), m,
+                      rs_.as<T>());
+        if (n) launch(k_colsq_weighted<T>, ceil_div((long long)n * 32, 256), 256, stream_, PAt_rowptr_.as<int>(),
+                      PAt_col_.as<int>(), PAt_pend_.as<int>(), (const T *)PAt_val_.as<T>(), (const T *)rs_.as<T>(), n,
+                      colsq_.as<T>());
+        GB_CUDA(cudaGetLastError());
+    }
+
     CsrDev<T> csrA() const { return csr(planA_, A_val_.as<T>()); }
     CsrDev<T> csrPAt() const { return csr(planPAt_, PAt_val_.as<T>()); }
 
     Vecs<T> vecs() const {
         Vecs<T> v;
         v.xy = xy_.as<T>();
+        v.dxy = dxy_.as<T>();
         v.xt = xt_.as<T>();
         v.pt = pt_.as<T>();
         v.z = z_.as<T>();
@@ -1099,12 +1397,15 @@ private:
         v.minv = minv_.as<T>();
         v.diagp = diagp_.as<T>();
         v.colsq = colsq_.as<T>();
+        v.rs = s_.rho_vector ? rs_.as<T>() : nullptr;
         v.pc = pc_.as<T>();
         v.kp = kp_.as<T>();
         v.r = r_.as<T>();
         v.yv = yv_.as<T>();
         v.D = D_.as<double>();
         v.E = E_.as<double>();
+        v.Dinv = Dinv_.as<double>();
+        v.Einv = Einv_.as<double>();
         v.x_out = x_out_.as<double>();
         v.y_out = y_out_.as<double>();
         v.z_out = z_out_.as<double>();
@@ -1146,6 +1447,10 @@ private:
     }
     void launch_check(const Vecs<T> &v, Status *st, cudaGraphConditionalHandle h, int use_h) {
         launch_smem(k_check_a<T>, gCa_, kThreads, kSmemD, stream_, csrA(), v, st, partials_.as<double>());
+        if (inf_on_) {
+            launch_smem(k_inf_a<T>, gIa_, kThreads, kSmemT, stream_, csrA(), v, st, partials_.as<double>());
+            launch_smem(k_inf_b<T>, gIb_, kThreads, kSmemT, stream_, csrPAt(), v, st, partials_.as<double>());
+        }
         launch_smem(k_check_b<T>, gCb_, kThreads, kSmemD, stream_, csrPAt(), v, st, partials_.as<double>(), policy(), h, use_h);
         GB_CUDA(cudaGetLastError());
     }
@@ -1174,8 +1479,8 @@ private:
 
     // Whole solve as one graph:
     //   reset -> WHILE(admm) { check_every x [pcg_init -> WHILE(pcg)
-    //   { p_t -> kp -> update } -> admm_update] -> check_a -> check_b
-    //   -> rho_apply } -> output
+    //   { p_t -> kp -> update } -> admm_update] -> check_a [-> inf_a ->
+    //   inf_b] -> check_b -> rho_apply } -> output
     void build_graph() {
         Vecs<T> v = vecs();
         Status *st = st_.as<Status>();
@@ -1201,6 +1506,10 @@ private:
             prev = add_kernel_smem(body, &nw, k_admm_update<T>, gAdmm_, kSmemT, A, v, st);
         }
         cudaGraphNode_t ca = add_kernel_smem(body, &prev, k_check_a<T>, gCa_, kSmemD, A, v, st, part);
+        if (inf_on_) {
+            ca = add_kernel_smem(body, &ca, k_inf_a<T>, gIa_, kSmemT, A, v, st, part);
+            ca = add_kernel_smem(body, &ca, k_inf_b<T>, gIb_, kSmemT, PAt, v, st, part);
+        }
         cudaGraphNode_t cb = add_kernel_smem(body, &ca, k_check_b<T>, gCb_, kSmemD, PAt, v, st, part, policy(), hA, 1);
         add_kernel(body, &cb, k_rho_apply<T>, gridN_, v, (const Status *)st);
         GB_CUDA(cudaGraphInstantiate(&exec_, graph_, 0));
@@ -1239,12 +1548,14 @@ private:
     cudaStream_t stream_;
     double c_ = 1.0;
     DevBuf A_rowptr_, A_col_, A_val_, PAt_rowptr_, PAt_col_, PAt_val_, PAt_pend_;
-    DevBuf D_, E_;
+    DevBuf D_, E_, Dinv_, Einv_;
+    DevBuf dxy_, rs_;
     DevBuf xy_, xt_, pt_, z_, zt_, l_, u_, q_, minv_, diagp_, colsq_, pc_, kp_, r_, yv_, tmp_n_, tmp_nm_;
     DevBuf x_out_, y_out_, z_out_;
     DevBuf partials_, st_, st2_, policy_;
     DevPlan planA_, planPAt_;
-    int gPt_ = 1, gAdmm_ = 1, gCa_ = 1, gKp_ = 1, gInit_ = 1, gCb_ = 1, gridN_ = 1, gridVec_ = 1;
+    int gPt_ = 1, gAdmm_ = 1, gCa_ = 1, gKp_ = 1, gInit_ = 1, gCb_ = 1, gIa_ = 1, gIb_ = 1, gridN_ = 1, gridVec_ = 1;
+    bool inf_on_ = false;
     static constexpr size_t kSmemT = rowblock_smem<T, T>();
     static constexpr size_t kSmemD = rowblock_smem<T, double>();
     cudaGraph_t graph_ = nullptr;

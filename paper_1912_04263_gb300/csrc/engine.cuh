@@ -34,6 +34,10 @@ public:
     virtual int solve() = 0;                                   // returns status
     virtual void update_rho(double rho) = 0;
     virtual void warm_start(const double *x, const double *y) = 0;
+    // parametric updates (scaled with the set-up's D, E, c); inputs on the
+    // host or the device as settings.input_location says
+    virtual void update_lin_cost(const double *q) = 0;
+    virtual void update_bounds(const double *l, const double *u) = 0;
     virtual void get_solution(double *x, double *y, double *z, bool device) = 0;
     virtual void fill_info(gbosqp_info &info) = 0;
     virtual void get_scaling(double *D, double *E, double *c) = 0;

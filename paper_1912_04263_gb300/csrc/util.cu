@@ -60,10 +60,11 @@ static int group_width(long long avg) {
 
 // Cut the rows into work items: runs of consecutive rows with at most kCap
 // nonzeros and few enough rows that the CTA's lane groups reduce them in one
-// round (rows x group width <= kThreads: each row's epilogue, a chain of
-// dependent memory accesses, runs once per thread), so that items of short
-// rows cost about as much as items of long ones; a row longer than kCap
-// becomes ceil(len / kCap) pieces of nearly equal length.
+// round when rows are short (group width <= 4: the cost is each row's
+// epilogue, a chain of dependent memory accesses) and in two rounds
+// otherwise (the cost is summing the row), so that items cost about the
+// same; a row longer than kCap becomes ceil(len / kCap) pieces of nearly
+// equal length.
 HostPlan build_plan(const std::vector<int> &rp) {
     HostPlan hp;
     const int nrows = (int)rp.size() - 1;
@@ -88,7 +89,9 @@ HostPlan build_plan(const std::vector<int> &rp) {
             const long long l = (long long)rp[r + 1] - rp[r];
             if (l > kCap || tot + l > kCap) break;
             const long long rows = r - r0 + 1;
-            if (rows > 1 && rows * group_width((tot + l) / rows) > (long long)kThreads) break;
+            const int gw = group_width((tot + l) / rows);
+            const long long rounds = gw <= 4 ? 1 : 2;  // short rows: one epilogue per thread
+            if (rows > 1 && rows * gw > rounds * kThreads) break;
             tot += l;
             ++r;
         }

@@ -1,7 +1,9 @@
 """Train the learned rho / PCG-tolerance policy on trajectories the solver
 generates itself, on the GPU, and evaluate it on held-out QPs.
 
-The policy is not part of the paper.  Labels come from a short lookahead at
+The policy is not part of the paper.  Training problems mix the random,
+Lasso and portfolio families (seeds disjoint from every evaluation seed).
+Labels come from a short lookahead at
 every rho decision (every 10 ADMM iterations): from the current state the
 solver runs H iterations for each candidate (rho multiplier, lambda) pair,
 and the label is the candidate with the largest progress per unit of work,
@@ -163,40 +165,73 @@ def summarize(rows) -> dict:
     return out
 
 
+def training_problem(i: int, rng):
+    """Training problem i: a random QP, a Lasso QP or a portfolio QP (in
+    proportions 2 : 1 : 1), sizes drawn from rng, seed TRAIN_SEED0 + i."""
+    seed = TRAIN_SEED0 + i
+    kind = ("random", "random", "lasso", "portfolio")[i % 4]
+    if kind == "random":
+        n = int(rng.integers(500, 2501))
+        return f"random_{n}", qpgen.random_qp(n, 10 * n, seed)
+    if kind == "lasso":
+        f = int(rng.integers(50, 401))
+        return f"lasso_{f}x{20 * f}", qpgen.lasso_qp(f, 20 * f, seed)
+    na = int(rng.integers(2000, 10001))
+    k = int(rng.integers(20, 101))
+    return f"portfolio_{na}x{k}", qpgen.portfolio_qp(na, k, seed)
+
+
+def eval_problems(args):
+    out = [(f"random_{args.eval_n}_s{EVAL_SEED0 + i}", qpgen.random_qp(args.eval_n, 10 * args.eval_n, EVAL_SEED0 + i))
+           for i in range(args.eval)]
+    out += [(f"random_5000_s{EVAL_SEED0 + 1000 + i}", qpgen.random_qp(5000, 50000, EVAL_SEED0 + 1000 + i))
+            for i in range(args.eval_large)]
+    out += [(f"lasso_300x6000_s{EVAL_SEED0 + 2000 + i}", qpgen.lasso_qp(300, 6000, EVAL_SEED0 + 2000 + i))
+            for i in range(args.eval_family)]
+    out += [(f"portfolio_8000x80_s{EVAL_SEED0 + 3000 + i}", qpgen.portfolio_qp(8000, 80, EVAL_SEED0 + 3000 + i))
+            for i in range(args.eval_family)]
+    if args.eval_full:
+        out += [("lasso_1000x100000_s0", qpgen.lasso_qp(1000, 100000, 0)),
+                ("portfolio_100000x1000_s0", qpgen.portfolio_qp(100000, 1000, 0)),
+                ("random_20000x200000_s0", qpgen.random_qp(20000, 200000, 0, p_density=5e-4, a_density=0.01))]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "policy"))
     ap.add_argument("--train", type=int, default=240, help="training trajectories")
-    ap.add_argument("--n-min", type=int, default=500)
-    ap.add_argument("--n-max", type=int, default=2000)
     ap.add_argument("--eval", type=int, default=24, help="held-out problems at n = --eval-n")
     ap.add_argument("--eval-n", type=int, default=3000)
     ap.add_argument("--eval-large", type=int, default=4, help="held-out problems at n = 5000")
     ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--eval-family", type=int, default=6, help="held-out Lasso and portfolio problems each")
+    ap.add_argument("--eval-full", action="store_true", help="also the full-size Lasso, portfolio, random QPs")
     args = ap.parse_args()
     os.makedirs(args.out, exist_ok=True)
     t0 = time.time()
     rng = np.random.default_rng(12345)
-    sizes = rng.integers(args.n_min, args.n_max + 1, size=args.train)
     samples = []
-    for i, n in enumerate(sizes):
-        qp = qpgen.random_qp(int(n), 10 * int(n), TRAIN_SEED0 + i)
+    for i in range(args.train):
+        name, qp = training_problem(i, rng)
         samples.extend(trajectory(qp))
         if i % 20 == 0:
-            print(f"trajectory {i}/{args.train} n={n} samples={len(samples)} t={time.time() - t0:.0f}s", flush=True)
+            print(f"trajectory {i}/{args.train} {name} samples={len(samples)} t={time.time() - t0:.0f}s", flush=True)
     S = np.array(samples, np.float64)
     np.save(os.path.join(args.out, "samples.npy"), S)
     p, hist = train(S, steps=args.steps)
     path = os.path.join(args.out, "rho_policy.bin")
     gb.save_policy(path, p)
     print(f"trained on {len(S)} samples: loss {hist[:50].mean():.4f} -> {hist[-50:].mean():.4f}", flush=True)
-    probs = [(f"random_{args.eval_n}_s{EVAL_SEED0 + i}", qpgen.random_qp(args.eval_n, 10 * args.eval_n, EVAL_SEED0 + i))
-             for i in range(args.eval)]
-    probs += [(f"random_5000_s{EVAL_SEED0 + 1000 + i}", qpgen.random_qp(5000, 50000, EVAL_SEED0 + 1000 + i))
-              for i in range(args.eval_large)]
-    rows = evaluate(p, probs)
+    rows = evaluate(p, eval_problems(args))
     summary = summarize(rows)
-    report = {"train_trajectories": int(args.train), "train_n_range": [args.n_min, args.n_max],
+    for fam in ("random", "lasso", "portfolio"):
+        sub = [r for r in rows if r["problem"].startswith(fam)]
+        if sub:
+            summary["family_" + fam] = summarize(sub)
+    report = {"train_trajectories": int(args.train),
+              "train_families": "random n in [500, 2500] (half), Lasso f in [50, 400] x 20f, portfolio "
+                                "[2000, 10000] assets x [20, 100] factors",
               "samples": int(len(S)), "loss_first": float(hist[:50].mean()), "loss_last": float(hist[-50:].mean()),
               "label_mult_hist": np.histogram(S[:, 4], bins=[-3, -1.7, -0.5, 0.5, 1.7, 3])[0].tolist(),
               "summary": summary, "rows": rows, "seconds": time.time() - t0}
