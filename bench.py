@@ -153,8 +153,9 @@ def gpu_arm(args) -> None:
         dist.barrier()
     import qpgen
     from paper_1912_04263_gb300 import binding as gb
+    from paper_1912_04263_gb300 import replicas
 
-    qp = qpgen.by_name(args.workload, args.seed + rank)
+    qp = qpgen.by_name(args.workload, replicas.replica_seed(args.seed, rank))
     n, m = qp.n, qp.m
     dev = torch.device("cuda", local)
     P, A = qp.P.tocsr(), qp.A.tocsr()
@@ -249,11 +250,7 @@ def gpu_arm(args) -> None:
         return ms, infos, stats, [h for h, _ in hs]
 
     def maxrank(v):
-        if not dist:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replicas.max_over_ranks(v, dist, dev)
 
     # warm-up
     for _ in range(args.warmup):
@@ -322,7 +319,7 @@ def gpu_arm(args) -> None:
                 traffic = float(parts[2])
     out = {
         "metric": METRIC,
-        "value": world * 1000.0 / ms_step,
+        "value": replicas.job_throughput(args.steps, world, ms_step * args.steps / 1000.0),
         "unit": "solves/s",
         "n_gpus": world,
         "steps": args.steps,
@@ -354,7 +351,7 @@ def gpu_arm(args) -> None:
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": round(gbs[dominant] / hbm, 4),
                      "traffic": traffic,
                      "algorithmic_bytes": algorithmic_bytes(dominant, n_, m_, nnz_pat if dominant == "pcg_kapply" else nnz_a)},
-        "e2e": {"value": world * 1000.0 / e2e_step, "unit": "solves/s", "ms_per_step": e2e_step,
+        "e2e": {"value": replicas.job_throughput(1, world, e2e_step / 1000.0), "unit": "solves/s", "ms_per_step": e2e_step,
                 "h2d_bytes_per_step": int(h2d_bytes), "d2h_bytes_per_step": int(d2h_bytes)},
         "clocks": clocks,
         "gpu_launches": launches,

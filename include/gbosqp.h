@@ -296,13 +296,15 @@ int gbosqp_admm_iterations(gbosqp_handle *h, int32_t k, int32_t *pcg_per_iter);
 /* Evaluate the termination check at the current state and write, in order:
  * r_prim, r_dual, eps_prim, eps_dual (unscaled, Section 3.1), the scaled
  * r_prim, r_dual, ||Ax||, ||z||, ||Px||, ||A'y||, ||q|| (used by the rho
- * rule and the PCG tolerance), the objective, and 4 reserved zeros. */
+ * rule and the PCG tolerance), the objective, the rho the residual-ratio
+ * rule would set from this check, and 3 reserved zeros. */
 int gbosqp_check(gbosqp_handle *h, double out[GBOSQP_CHECK_FIELDS]);
 
 /* ---- learned rho policy (not in the paper) ----------------------------- *
- * A 4-64-64-2 MLP (ReLU) proposes, at every rho decision, a log multiplier
- * for rho (output 0, clamped) and a log factor for the PCG tolerance weight
- * lambda (output 1, used when the last parameter is 1).  Its features are
+ * A 4-64-64-2 MLP (ReLU) proposes, at every rho decision, rho as the
+ * residual-ratio rule's rho times exp(output 0) (output 0 clamped; a zero
+ * output reproduces the ratio rule) and a log factor for the PCG tolerance
+ * weight lambda (output 1, used when the last parameter is 1).  Its features are
  * log ||r_prim||, log ||r_dual|| (scaled problem), log rho and
  * log(1 + PCG steps since the last decision); it sees (f - mean) / std.
  * Operands are rounded to BF16 (weights, inputs, hidden activations and, in
@@ -332,6 +334,13 @@ int gbosqp_mlp_train(float *params, const float *features, const float *targets,
  * checks of a handle and the current PCG tolerance eps (> 0) until the next
  * check (step-level call, e.g. for policy lookahead). */
 int gbosqp_set_pcg_lambda(gbosqp_handle *h, double lambda, double eps);
+
+/* Make the next osqp_solve continue from the handle's current state: the
+ * iterates (e.g. those given to gbosqp_set_iterates), rho, the PCG tolerance
+ * and lambda are kept; the iteration count starts from 0, so the next rho
+ * decision comes rho_every iterations later (step-level call, e.g. for
+ * rollouts that score a rho choice by the rest of the solve). */
+int gbosqp_resume(gbosqp_handle *h);
 
 /* Kernel selectors for gbosqp_bench_kernel. */
 #define GBOSQP_K_PCG_DIRECTION 0  /* p = -M^{-1}r + beta p, t = rho A p (SpMV A)        */

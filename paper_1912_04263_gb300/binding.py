@@ -104,6 +104,7 @@ def lib():
         "gbosqp_mlp_train": (i32, [_P, _P, _P, _P, i32, _P, i32, i32, ctypes.c_float, _P]),
         "gbosqp_set_pcg_lambda": (i32, [_P, dbl, dbl]),
         "osqp_update_lin_cost": (i32, [_P, _P]),
+        "gbosqp_resume": (i32, [_P]),
         "osqp_update_bounds": (i32, [_P, _P, _P]),
     }
     for name, (res, args) in sig.items():
@@ -218,6 +219,12 @@ def osqp_warm_start(h, x=None, y=None) -> None:
     xv = None if x is None else _vec(x, n)
     yv = None if y is None else _vec(y, m)
     _check(h, lib().osqp_warm_start(h, _ptr(xv), _ptr(yv)))
+
+
+def gbosqp_resume(h) -> None:
+    """The next solve continues from the current iterates, rho, PCG
+    tolerance and lambda."""
+    _check(h, lib().gbosqp_resume(h))
 
 
 def osqp_update_lin_cost(h, q) -> None:
@@ -419,7 +426,7 @@ def load_policy(path: str) -> np.ndarray:
 
 
 CHECK_NAMES = ["r_prim", "r_dual", "eps_prim", "eps_dual", "r_prim_s", "r_dual_s", "norm_Ax_s", "norm_z_s",
-               "norm_Px_s", "norm_Aty_s", "norm_q_s", "obj"]
+               "norm_Px_s", "norm_Aty_s", "norm_q_s", "obj", "rho_ratio"]
 
 
 def gbosqp_check(h) -> dict:

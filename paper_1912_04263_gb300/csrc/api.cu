@@ -366,6 +366,15 @@ int gbosqp_bench_kernel(gbosqp_handle *h, int kernel, int32_t reps, double *avg_
     API_CATCH(h)
 }
 
+int gbosqp_resume(gbosqp_handle *h) {
+    if (!h || !h->eng) return GBOSQP_ERR_INVALID_ARG;
+    API_TRY
+    GB_CUDA(cudaSetDevice(h->s.device));
+    h->eng->resume();
+    return GBOSQP_OK;
+    API_CATCH(h)
+}
+
 int gbosqp_set_pcg_lambda(gbosqp_handle *h, double lambda, double eps) {
     if (!h || !h->eng) return GBOSQP_ERR_INVALID_ARG;
     if (!(lambda > 0.0 && lambda < 1.0)) return fail_code(h, GBOSQP_ERR_INVALID_ARG, "lambda must be in ]0, 1[");

@@ -68,6 +68,15 @@ constexpr int kWarps = kThreads / 32;
 #define GB_CAP 2048
 #endif
 constexpr int kCap = GB_CAP;              // max nonzeros per work item
+// Fixed cost of a work item in nonzero-equivalents (descriptor, barriers,
+// epilogue latency), used to give every CTA an equal share of the work.
+// Measured on GB300 an item costs about the same whatever its nonzero
+// count (items of 512 and of 2048 nonzeros take about equally long), so the
+// fixed part dominates: CTAs get equal item counts, nonzeros break ties.
+#ifndef GB_ITEM_COST
+#define GB_ITEM_COST (1 << 20)
+#endif
+constexpr long long kItemCost = GB_ITEM_COST;
 constexpr int kPerThread = kCap / kThreads;
 constexpr double kInf = 1e20;             // |bound| >= kInf is infinite
 
@@ -92,6 +101,16 @@ struct HostPlan {
 };
 HostPlan build_plan(const std::vector<int> &rowptr);
 
+// Assignment of the items to `grid` CTAs: CTA b takes the contiguous range
+// [part[b], part[b+1]); every CTA gets at least one item (grid <= items) and
+// the ranges have about equal cost (nonzeros + kItemCost per item).
+// lr_cta[l] holds the first and last CTA with a piece of long row l.
+struct HostPartition {
+    std::vector<int> part;
+    std::vector<int2> lr_cta;
+};
+HostPartition partition_items(const HostPlan &hp, int grid);
+
 // Device view of a CSR matrix with its plan.  pend (optional) splits each
 // row into two segments [rowptr[r], pend[r]) and [pend[r], rowptr[r+1]).
 template <class T>
@@ -106,6 +125,8 @@ struct CsrDev {
     const LongRow *longrows = nullptr;
     int *lr_count = nullptr;     // one ticket counter per long row (zeroed)
     double *lr_part = nullptr;   // 2 partial sums per item
+    const int *part = nullptr;   // grid + 1 item boundaries (see partition_items)
+    const int2 *lr_cta = nullptr;  // first and last CTA of each long row
     int *err = nullptr;          // set to 1 if a bulk copy wait timed out
 };
 
@@ -117,7 +138,9 @@ struct Status {
     // problem constants
     double sigma, alpha, eps_abs, eps_rel, lambda, eps_min, rho_min, rho_max;
     double rho0, c, cinv, eps0, qnorm_s, qnorm_u;
-    int n, m, max_iter, max_cg, check_every, rho_every, policy, warm;
+    int n, m, max_iter, max_cg, check_every, rho_every, policy;
+    int warm;  // 0: cold start; 1: start from the iterates (warm start, rho kept);
+               // 2: resume (also keep the PCG tolerance and lambda)
     // evolving
     double rho, eps_pcg;
     double ry, pkp, alpha_cg, beta, rnorm;
@@ -141,6 +164,7 @@ struct Status {
                       // q_bar'dx_bar, ||D dx_bar||
     int inf_on;
     int keep_warm;  // 1: each solve starts from the previous solve's iterates
+    double lambda0; // the settings' PCG tolerance weight (a solve starts with it)
     // last-block tickets, one per kernel kind
     unsigned int tickets[16];
 };
@@ -289,14 +313,69 @@ __device__ __forceinline__ double to_acc<double, float>(float v) { return f2d_ex
 // groups leave their row sums in rsum and the rows are then finished one
 // per thread, so that the epilogue (a chain of dependent loads, and in the
 // FP64 checks the expensive arithmetic) runs on all lanes instead of on one
-// lane per group; rows are taken in chunks of kThreads.
+// lane per group; rows are taken in chunks of kThreads.  For FP64 sums the
+// G lane partials of a row go through shared memory (over the products,
+// once they are read) and one thread adds them in lane order: one FP64 add
+// per partial instead of log2(G) shuffle rounds on every lane, the FP64
+// pipe being narrow on this GPU.
 template <int G, bool SPLIT, class Acc, class T, class Epi, class RedT>
-__device__ __forceinline__ void reduce_rows(const CsrDev<T> &M, const Item &it, const T *sprod, Epi &epi,
+__device__ __forceinline__ void reduce_rows(const CsrDev<T> &M, const Item &it, T *sprod, Epi &epi,
                                             RedT &red, Acc (*rsum)[kThreads]) {
     const int lane_g = threadIdx.x & (G - 1);
     const int grp = threadIdx.x / G;
     constexpr int ngrp = kThreads / G;
+    constexpr int kParts = SPLIT ? 2 : 1;
     const int R = it.r1 - it.r0;
+    // transposed FP64 reduction when every partial of the item fits over the
+    // products (kCap * sizeof(T) bytes)
+    constexpr bool kFp64 = sizeof(Acc) == 8 && G > 1;
+    constexpr int kRounds = kFp64 ? 4 : 1;  // lane-group rounds kept in registers
+    const int nb = (R + ngrp - 1) / ngrp;
+    const bool transposed =
+        kFp64 && nb <= kRounds && R * G * kParts * (int)sizeof(Acc) <= kCap * (int)sizeof(T);
+    if (transposed) {
+        Acc p1[kRounds], p2[kRounds];
+#pragma unroll
+        for (int b = 0; b < kRounds; ++b) {
+            p1[b] = Acc(0);
+            p2[b] = Acc(0);
+            const int lr = b * ngrp + grp;
+            if (b < nb && lr < R) {
+                const int r = it.r0 + lr;
+                const int a = __ldg(M.rowptr + r) - it.k0;
+                const int e1 = __ldg(M.rowptr + r + 1) - it.k0;
+                if (SPLIT) {
+                    const int sp = __ldg(M.pend + r) - it.k0;
+                    for (int e = a + lane_g; e < e1; e += G) {
+                        if (e < sp) p1[b] += to_acc<Acc>(sprod[e]); else p2[b] += to_acc<Acc>(sprod[e]);
+                    }
+                } else {
+                    for (int e = a + lane_g; e < e1; e += G) p1[b] += to_acc<Acc>(sprod[e]);
+                }
+            }
+        }
+        __syncthreads();  // every product read: the buffer takes the partials
+        Acc *lp = reinterpret_cast<Acc *>(sprod);
+#pragma unroll
+        for (int b = 0; b < kRounds; ++b) {
+            const int lr = b * ngrp + grp;
+            if (b < nb && lr < R) {
+                lp[lr * G + lane_g] = p1[b];
+                if (SPLIT) lp[R * G + lr * G + lane_g] = p2[b];
+            }
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < R; t += kThreads) {
+            Acc s1 = Acc(0), s2 = Acc(0);
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                s1 += lp[t * G + g];
+                if (SPLIT) s2 += lp[R * G + t * G + g];
+            }
+            epi.row(it.r0 + t, s1, s2, red);
+        }
+        return;
+    }
     for (int c0 = 0; c0 < R; c0 += (G > 1 ? kThreads : R)) {
         const int cn = G > 1 ? min(kThreads, R - c0) : R;
         for (int base = 0; base < cn; base += ngrp) {
@@ -361,25 +440,75 @@ __device__ __forceinline__ void load_item(const CsrDev<T> &M, const Item &it, T 
     }
 }
 
+// Long-row ends pending in a CTA before they are finished together.
+constexpr int kRowBatch = 32;
+
+// Finish the pending long-row ends of a CTA, one per thread: add the warp
+// partials in warp order, then either consume the row (all its pieces in
+// this CTA) or publish this CTA's partial and, if this CTA is the last of
+// the row's CTAs to arrive, add every CTA's partial in CTA order and
+// consume the row.  Called by every thread of the CTA (it synchronises).
+template <class Acc, class T, class Epi, class RedT>
+__device__ __forceinline__ void finish_long_rows(const CsrDev<T> &M, int i0, int nq, const int *qlr,
+                                                 Acc (*qsum)[2][kWarps], Epi &epi, RedT &red) {
+    __syncthreads();
+    if ((int)threadIdx.x < nq) {
+        const int q = threadIdx.x;
+        double a1 = 0.0, a2 = 0.0;
+        for (int w = 0; w < kWarps; ++w) {
+            a1 += (double)qsum[q][0][w];
+            a2 += (double)qsum[q][1][w];
+        }
+        const int lr = qlr[q];
+        const LongRow L = M.longrows[lr];
+        const int row = M.items[L.first_item].r0;
+        const int first = L.first_item;
+        const int2 cr = M.lr_cta[lr];  // CTAs holding pieces of the row
+        if (cr.x == cr.y) {
+            epi.row(row, Acc(a1), Acc(a2), red);
+        } else {
+            const int slot = max(first, i0);  // this CTA's first piece of the row
+            M.lr_part[2 * (size_t)slot] = a1;
+            M.lr_part[2 * (size_t)slot + 1] = a2;
+            __threadfence();
+            const int t = atomicAdd(M.lr_count + lr, 1);
+            if (t == cr.y - cr.x) {
+                __threadfence();
+                double t1 = 0.0, t2 = 0.0;
+                for (int cc = cr.x; cc <= cr.y; ++cc) {
+                    const int sl = max(first, M.part[cc]);
+                    t1 += __ldcg(M.lr_part + 2 * (size_t)sl);
+                    t2 += __ldcg(M.lr_part + 2 * (size_t)sl + 1);
+                }
+                M.lr_count[lr] = 0;
+                epi.row(row, Acc(t1), Acc(t2), red);
+            }
+        }
+    }
+    __syncthreads();
+}
+
 // Process the contiguous range of items assigned to this CTA.  Each step
 // prefetches the next item's values and columns into registers, then
 // multiplies the current item by the gathered vector in the working
 // precision (into shared memory) and reduces its rows with lane groups sized
 // to the mean row length, accumulating in Acc (FP64 for the termination
 // check: FP32 products summed in FP64).
-// Consecutive pieces of a long row accumulate per thread and are reduced
-// once; a long row that crosses a CTA boundary is combined by the last of
-// its contributors, in CTA order.  gather(c) returns the vector entry for
+// Consecutive pieces of a long row accumulate per thread; at the row's end
+// (in this CTA) the warps leave their partials in shared memory and up to
+// kRowBatch such row ends are finished together (finish_long_rows); a long
+// row that crosses a CTA boundary is combined by the last of its
+// contributors, in CTA order.  gather(c) returns the vector entry for
 // column c in the accumulation type; epi.row(r, s1, s2, red) consumes rows.
 template <class Acc, bool SPLIT, class T, class Gather, class Epi, class RedT>
 __device__ __forceinline__ bool run_items(const CsrDev<T> &M, const Gather &gather, Epi &epi, RedT &red) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sprod = reinterpret_cast<T *>(smem_raw);
-    __shared__ Acc wsum[2][kWarps];
     __shared__ Acc rsum[SPLIT ? 2 : 1][kThreads];
-    const int Q = (M.nitems + (int)gridDim.x - 1) / (int)gridDim.x;
-    const int i0 = (int)blockIdx.x * Q;
-    const int i1 = min(M.nitems, i0 + Q);
+    __shared__ Acc qsum[kRowBatch][2][kWarps];
+    __shared__ int qlr[kRowBatch];
+    const int i0 = M.part[blockIdx.x];
+    const int i1 = M.part[blockIdx.x + 1];
     T va[kPerThread], vb[kPerThread];
     int ca[kPerThread], cb[kPerThread];
     // descriptors run one item ahead of the value/column registers
@@ -390,6 +519,7 @@ __device__ __forceinline__ bool run_items(const CsrDev<T> &M, const Gather &gath
     }
     if (i0 + 1 < i1) nx = M.items[i0 + 1];
     Acc ps1 = Acc(0), ps2 = Acc(0);  // running sums of a long row's pieces
+    int nq = 0;                      // pending long-row ends (uniform in the CTA)
     for (int itx = i0; itx < i1; ++itx) {
         const Item it = cur;
         const bool has_next = itx + 1 < i1;
@@ -436,37 +566,15 @@ __device__ __forceinline__ bool run_items(const CsrDev<T> &M, const Gather &gath
                     s2 += __shfl_down_sync(0xffffffffu, s2, o);
                 }
                 const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-                if (lane == 0) { wsum[0][warp] = s1; wsum[1][warp] = s2; }
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    double a1 = 0.0, a2 = 0.0;
-                    for (int w = 0; w < kWarps; ++w) { a1 += (double)wsum[0][w]; a2 += (double)wsum[1][w]; }
-                    const int lr = -(it.r1 + 1);
-                    const LongRow L = M.longrows[lr];
-                    const int first = L.first_item, last = L.first_item + L.npieces - 1;
-                    const int c0 = first / Q, c1 = last / Q;  // CTA ranges covering the row
-                    if (c0 == c1) {
-                        epi.row(row, Acc(a1), Acc(a2), red);
-                    } else {
-                        const int slot = max(first, i0);  // this CTA's first piece of the row
-                        M.lr_part[2 * (size_t)slot] = a1;
-                        M.lr_part[2 * (size_t)slot + 1] = a2;
-                        __threadfence();
-                        const int t = atomicAdd(M.lr_count + lr, 1);
-                        if (t == c1 - c0) {
-                            __threadfence();
-                            double t1 = 0.0, t2 = 0.0;
-                            for (int cc = c0; cc <= c1; ++cc) {
-                                const int sl = max(first, cc * Q);
-                                t1 += __ldcg(M.lr_part + 2 * (size_t)sl);
-                                t2 += __ldcg(M.lr_part + 2 * (size_t)sl + 1);
-                            }
-                            M.lr_count[lr] = 0;
-                            epi.row(row, Acc(t1), Acc(t2), red);
-                        }
-                    }
+                if (lane == 0) {
+                    qsum[nq][0][warp] = s1;
+                    qsum[nq][1][warp] = s2;
                 }
-                __syncthreads();
+                if (threadIdx.x == 0) qlr[nq] = -(it.r1 + 1);
+                if (++nq == kRowBatch) {
+                    finish_long_rows<Acc>(M, i0, nq, qlr, qsum, epi, red);
+                    nq = 0;
+                }
             }
         }
         if (has_next) {
@@ -479,6 +587,7 @@ __device__ __forceinline__ bool run_items(const CsrDev<T> &M, const Gather &gath
             nx = nx2;
         }
     }
+    if (nq > 0) finish_long_rows<Acc>(M, i0, nq, qlr, qsum, epi, red);
     return true;
 }
 

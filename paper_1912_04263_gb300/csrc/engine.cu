@@ -12,9 +12,10 @@
 //                             t0 = rho (A x~ - z) + y for the next PCG init
 //   pt  = [p ; t]    (n+m)    PCG direction p and t = rho A p
 //   dxy = [dx ; dy]  (n+m)    x^k - x^(k-1) and y^k - y^(k-1) (scaled)
-//   z, zt (= A x~), l, u (m); q, minv, diagP, colsq, pc (previous p),
-//   kp (K p), r, yv (= M^{-1} r) (n); D, E and their reciprocals (double)
-//   for unscaling.
+//   z, zt (= A x~), l, u (m); q, minv, diagP, colsq, kp (K p), r (n);
+//   ypc = (yv, pc) pairs (n): yv = M^{-1} r and pc = the previous p,
+//   interleaved so that one load gathers both; D, E and their reciprocals
+//   (double) for unscaling.
 //
 // Kernels of one ADMM iteration (each row-block kernel streams one matrix):
 //   pcg_init   PAt: r = P x~ + sigma (x~ - x) + q + A' t0  (= K x~ - b),
@@ -42,6 +43,7 @@
 #include <cstddef>
 #include <initializer_list>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <string>
 #include <tuple>
@@ -55,11 +57,27 @@ namespace gb {
 
 namespace {
 
+// (M^{-1} r, previous direction) pairs, stored interleaved so that the
+// direction kernel's gather of p = -M^{-1} r + beta p_prev is one load
+template <class T>
+struct Pair;
+template <>
+struct Pair<float> {
+    using type = float2;
+};
+template <>
+struct Pair<double> {
+    using type = double2;
+};
+template <class T>
+using pair_t = typename Pair<T>::type;
+
 template <class T>
 struct Vecs {
     T *xy, *xt, *pt, *dxy;
     T *z, *zt, *l, *u;
-    T *q, *minv, *diagp, *colsq, *pc, *kp, *r, *yv;
+    T *q, *minv, *diagp, *colsq, *kp, *r;
+    pair_t<T> *ypc;  // (yv = M^{-1} r, pc = previous p) per variable
     const T *rs;  // R = rho diag(rs), eq. (rho_vec): 1e3 on rows with l = u, else 1;
                   // nullptr for R = rho I (Section 5.3)
     const double *D, *E, *Dinv, *Einv;
@@ -101,9 +119,12 @@ struct GatherVec {
 
 template <class T>
 struct GatherDir {  // p = -yv + beta * p_prev
-    const T *yv, *pc;
+    const pair_t<T> *ypc;
     T beta;
-    __device__ __forceinline__ T operator()(int c) const { return -__ldg(yv + c) + beta * __ldg(pc + c); }
+    __device__ __forceinline__ T operator()(int c) const {
+        const pair_t<T> w = __ldg(ypc + c);
+        return -w.x + beta * w.y;
+    }
 };
 
 // ------------------------------------------------------------ kernels
@@ -123,7 +144,7 @@ __global__ void __launch_bounds__(kThreads) k_reset(Vecs<T> v, Status *st, cudaG
                 v.xt[i] = T(0);
             }
             v.minv[i] = T(1.0 / ((double)v.diagp[i] + sigma + rho * (double)v.colsq[i]));
-            v.pc[i] = T(0);
+            v.ypc[i].y = T(0);
         }
         if (i < m && !warm) {
             v.xy[n + i] = T(0);
@@ -137,7 +158,10 @@ __global__ void __launch_bounds__(kThreads) k_reset(Vecs<T> v, Status *st, cudaG
         st->k = 0;
         st->cg_total = 0;
         st->status = 0;
-        st->eps_pcg = st->eps0;
+        if (st->warm != 2) {
+            st->eps_pcg = st->eps0;
+            st->lambda = st->lambda0;
+        }
         st->rho_updates = 0;
         st->rho_changed = 0;
         st->fallbacks = 0;
@@ -161,8 +185,7 @@ struct EpiInit {
         const T r = s1 + sigma * (v.xt[i] - v.xy[i]) + v.q[i];
         const T y = v.minv[i] * r;
         v.r[i] = r;
-        v.yv[i] = y;
-        v.pc[i] = T(0);
+        v.ypc[i] = pair_t<T>{y, T(0)};
         red.s[0] += (double)r * (double)y;
         red.m[0] = amax(red.m[0], absd(r));
     }
@@ -202,11 +225,13 @@ template <class T>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : 2) k_pcg_p_t(CsrDev<T> A, Vecs<T> v, const Status *st) {
     const T beta = T(st->beta);
     const int n = v.n;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        v.pt[i] = -v.yv[i] + beta * v.pc[i];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const pair_t<T> w = v.ypc[i];
+        v.pt[i] = -w.x + beta * w.y;
+    }
     EpiDir<T> epi{v.pt + n, v.rs, T(st->rho)};
     Red<0, 0> red;
-    run_items<T, false>(A, GatherDir<T>{v.yv, v.pc, beta}, epi, red);
+    run_items<T, false>(A, GatherDir<T>{v.ypc, beta}, epi, red);
 }
 
 // Kp = P p + sigma p + A' t;  p'Kp
@@ -259,8 +284,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(Vecs<T> v, Status *st, 
         const T y = v.minv[i] * r;
         v.xt[i] = x;
         v.r[i] = r;
-        v.yv[i] = y;
-        v.pc[i] = p;
+        v.ypc[i] = pair_t<T>{y, p};
         red.s[0] += (double)r * (double)y;
         red.m[0] = amax(red.m[0], absd(r));
     }
@@ -802,7 +826,8 @@ public:
         q_ = convert(std::move(sd.q), n);
         diagp_ = convert(std::move(sd.diagP), n);
         colsq_ = convert(std::move(sd.colsq), n);
-        for (DevBuf *b : {&minv_, &pc_, &kp_, &r_, &yv_, &tmp_n_}) b->alloc(sizeof(T) * std::max(n, 1));
+        for (DevBuf *b : {&minv_, &kp_, &r_, &tmp_n_}) b->alloc(sizeof(T) * std::max(n, 1));
+        ypc_.alloc(sizeof(pair_t<T>) * std::max(n, 1));
         tmp_nm_.alloc(sizeof(T) * std::max<size_t>(nm, 1));
         x_out_.alloc(sizeof(double) * std::max(n, 1));
         y_out_.alloc(sizeof(double) * std::max(m, 1));
@@ -841,6 +866,10 @@ public:
         gridVec_ = std::max(1, std::min(grid_for_n(n, kThreads), cap));
         gridN_ = std::max(1, std::min(grid_for_n(std::max(n, m), kThreads * 4), cap));
         const int maxgrid = std::max({gPt_, gAdmm_, gCa_, gKp_, gInit_, gCb_, gIa_, gIb_, gridN_, gridVec_});
+        const int gSpA = grid_for_items(planA_.nitems, (const void *)k_spmv<T, T>, kSmemT);
+        const int gSpP = grid_for_items(planPAt_.nitems, (const void *)k_spmv<T, T>, kSmemT);
+        for (int g : {gPt_, gAdmm_, gCa_, gIa_, gSpA}) part_for(planA_, g);
+        for (int g : {gKp_, gInit_, gCb_, gIb_, gSpP}) part_for(planPAt_, g);
         partials_.alloc(sizeof(double) * (size_t)maxgrid * 8);
         // status block
         Status h;
@@ -850,6 +879,7 @@ public:
         h.eps_abs = s.eps_abs;
         h.eps_rel = s.eps_rel;
         h.lambda = s.pcg_lambda;
+        h.lambda0 = s.pcg_lambda;
         h.eps_min = s.pcg_eps_min;
         h.rho_min = s.rho_min;
         h.rho_max = s.rho_max;
@@ -1086,8 +1116,8 @@ public:
         if (fp64acc) {
             // FP64 output through a double staging vector
             DevBuf yy(sizeof(double) * std::max(nout, 1));
-            CsrDev<T> M = csr(pl, val);
             const int g = grid_for_items(pl.nitems, (const void *)k_spmv_dbl<T>, kSmemD);
+            CsrDev<T> M = csr(pl, val, g);
             k_spmv_d(M, xT.as<T>(), yy.as<double>(), g);
             GB_CUDA(cudaMemcpyAsync(y, yy.p, sizeof(double) * nout, cudaMemcpyDeviceToHost, stream_));
         } else {
@@ -1214,7 +1244,7 @@ public:
         Status r = read_status(st2_);
         const double vals[GBOSQP_CHECK_FIELDS] = {r.r_prim, r.r_dual, r.eps_prim, r.eps_dual, r.rp_s, r.rd_s,
                                                   r.ax_s,   r.z_s,    r.px_s,     r.aty_s,    r.qnorm_s, r.obj,
-                                                  0.0,      0.0,      0.0,        0.0};
+                                                  rho_ratio(&r), 0.0, 0.0,        0.0};
         std::memcpy(out, vals, sizeof(vals));
     }
 
@@ -1235,15 +1265,15 @@ public:
         GB_CUDA(cudaMemcpyAsync(save_zt.p, zt_.p, zt_.bytes, cudaMemcpyDeviceToDevice, stream_));
         auto one = [&]() {
             switch (kernel) {
-                case GBOSQP_K_PCG_DIRECTION: launch_smem(k_pcg_p_t<T>, gPt_, kThreads, kSmemT, stream_, csrA(), v, (const Status *)st); break;
-                case GBOSQP_K_PCG_KAPPLY: launch_smem(k_pcg_kp<T>, gKp_, kThreads, kSmemT, stream_, csrPAt(), v, st, partials_.as<double>()); break;
+                case GBOSQP_K_PCG_DIRECTION: launch_smem(k_pcg_p_t<T>, gPt_, kThreads, kSmemT, stream_, csrA(gPt_), v, (const Status *)st); break;
+                case GBOSQP_K_PCG_KAPPLY: launch_smem(k_pcg_kp<T>, gKp_, kThreads, kSmemT, stream_, csrPAt(gKp_), v, st, partials_.as<double>()); break;
                 case GBOSQP_K_PCG_UPDATE: launch(k_pcg_update<T>, gridVec_, kThreads, stream_, v, st, partials_.as<double>(), (cudaGraphConditionalHandle)0, 0); break;
-                case GBOSQP_K_PCG_INIT: launch_smem(k_pcg_init<T>, gInit_, kThreads, kSmemT, stream_, csrPAt(), v, st, partials_.as<double>(), (cudaGraphConditionalHandle)0, 0); break;
-                case GBOSQP_K_ADMM_UPDATE: launch_smem(k_admm_update<T>, gAdmm_, kThreads, kSmemT, stream_, csrA(), v, st); break;
-                case GBOSQP_K_CHECK_A: launch_smem(k_check_a<T>, gCa_, kThreads, kSmemD, stream_, csrA(), v, st, partials_.as<double>()); break;
-                case GBOSQP_K_CHECK_B: launch_smem(k_check_b<T>, gCb_, kThreads, kSmemD, stream_, csrPAt(), v, st, partials_.as<double>(), policy(), (cudaGraphConditionalHandle)0, 0); break;
-                case GBOSQP_K_INF_A: launch_smem(k_inf_a<T>, gIa_, kThreads, kSmemT, stream_, csrA(), v, st, partials_.as<double>()); break;
-                case GBOSQP_K_INF_B: launch_smem(k_inf_b<T>, gIb_, kThreads, kSmemT, stream_, csrPAt(), v, st, partials_.as<double>()); break;
+                case GBOSQP_K_PCG_INIT: launch_smem(k_pcg_init<T>, gInit_, kThreads, kSmemT, stream_, csrPAt(gInit_), v, st, partials_.as<double>(), (cudaGraphConditionalHandle)0, 0); break;
+                case GBOSQP_K_ADMM_UPDATE: launch_smem(k_admm_update<T>, gAdmm_, kThreads, kSmemT, stream_, csrA(gAdmm_), v, st); break;
+                case GBOSQP_K_CHECK_A: launch_smem(k_check_a<T>, gCa_, kThreads, kSmemD, stream_, csrA(gCa_), v, st, partials_.as<double>()); break;
+                case GBOSQP_K_CHECK_B: launch_smem(k_check_b<T>, gCb_, kThreads, kSmemD, stream_, csrPAt(gCb_), v, st, partials_.as<double>(), policy(), (cudaGraphConditionalHandle)0, 0); break;
+                case GBOSQP_K_INF_A: launch_smem(k_inf_a<T>, gIa_, kThreads, kSmemT, stream_, csrA(gIa_), v, st, partials_.as<double>()); break;
+                case GBOSQP_K_INF_B: launch_smem(k_inf_b<T>, gIb_, kThreads, kSmemT, stream_, csrPAt(gIb_), v, st, partials_.as<double>()); break;
                 default: fail(GBOSQP_ERR_INVALID_ARG, "unknown kernel selector");
             }
         };
@@ -1293,6 +1323,13 @@ public:
         return reps > 0 ? ms / reps : 0.0;
     }
 
+    void resume() override {
+        const int two = 2;
+        GB_CUDA(cudaMemcpyAsync((char *)st_.p + offsetof(Status, warm), &two, sizeof(int), cudaMemcpyHostToDevice,
+                                stream_));
+        GB_CUDA(cudaStreamSynchronize(stream_));
+    }
+
     void set_lambda(double lambda, double eps) override {
         GB_CUDA(cudaMemcpyAsync((char *)st_.p + offsetof(Status, lambda), &lambda, sizeof(double),
                                 cudaMemcpyHostToDevice, stream_));
@@ -1309,17 +1346,22 @@ public:
             fail(GBOSQP_ERR_UNSUPPORTED, "matrix needs " + std::to_string(pl.nitems) + " work items and " +
                                              std::to_string(pl.nlong) + " long rows; the allocation-free SpMV holds at most " +
                                              std::to_string(max_items) + " and " + std::to_string(max_long_rows));
-        CsrDev<T> M = csr(pl, isA ? A_val_.as<T>() : PAt_val_.as<T>());
+        const int g = grid_for_items(pl.nitems, (const void *)k_spmv<T, T>, kSmemT);
+        CsrDev<T> M = csr(pl, isA ? A_val_.as<T>() : PAt_val_.as<T>(), g);  // partition built at set-up
         M.lr_part = part;
         M.lr_count = count;
         if (pl.nlong > 0) GB_CUDA(cudaMemsetAsync(count, 0, sizeof(int) * (size_t)pl.nlong, stream_));
-        const int g = grid_for_items(pl.nitems, (const void *)k_spmv<T, T>, kSmemT);
         launch_smem(k_spmv<T, T>, g, kThreads, kSmemT, stream_, M, static_cast<const T *>(x), static_cast<T *>(y), T(1));
     }
 
 private:
+    struct PartDev {
+        DevBuf part, lr_cta;
+    };
     struct DevPlan {
         DevBuf items, longrows, count, part;
+        HostPlan host;
+        mutable std::map<int, PartDev> parts;  // by grid size
         int nitems = 0;
         int nrows = 0;
         int nlong = 0;
@@ -1335,7 +1377,8 @@ private:
     }
 
     void build_plan_dev(const std::vector<int> &rp, DevPlan &pl) {
-        HostPlan hp = build_plan(rp);
+        pl.host = build_plan(rp);
+        const HostPlan &hp = pl.host;
         pl.nitems = (int)hp.items.size();
         pl.nrows = (int)rp.size() - 1;
         pl.nlong = (int)hp.longrows.size();
@@ -1353,9 +1396,29 @@ private:
         GB_CUDA(cudaStreamSynchronize(stream_));
     }
 
-    CsrDev<T> csr(const DevPlan &pl, const T *val) const {
+    // item partition of a plan for a launch of `grid` CTAs (built once per
+    // grid size; kernels with the same grid share it)
+    const PartDev &part_for(const DevPlan &pl, int grid) const {
+        auto it = pl.parts.find(grid);
+        if (it != pl.parts.end()) return it->second;
+        HostPartition hp = partition_items(pl.host, grid);
+        PartDev d;
+        d.part.alloc(sizeof(int) * hp.part.size());
+        d.lr_cta.alloc(sizeof(int2) * std::max<size_t>(hp.lr_cta.size(), 1));
+        GB_CUDA(cudaMemcpyAsync(d.part.p, hp.part.data(), sizeof(int) * hp.part.size(), cudaMemcpyHostToDevice, stream_));
+        if (!hp.lr_cta.empty())
+            GB_CUDA(cudaMemcpyAsync(d.lr_cta.p, hp.lr_cta.data(), sizeof(int2) * hp.lr_cta.size(), cudaMemcpyHostToDevice,
+                                    stream_));
+        GB_CUDA(cudaStreamSynchronize(stream_));
+        return pl.parts.emplace(grid, std::move(d)).first->second;
+    }
+
+    CsrDev<T> csr(const DevPlan &pl, const T *val, int grid) const {
         const bool isA = &pl == &planA_;
+        const PartDev &pd = part_for(pl, grid);
         CsrDev<T> M;
+        M.part = pd.part.template as<int>();
+        M.lr_cta = pd.lr_cta.template as<int2>();
         M.nrows = pl.nrows;
         M.ncols = isA ? n : n + m;
         M.rowptr = (isA ? A_rowptr_ : PAt_rowptr_).template as<int>();
@@ -1380,8 +1443,8 @@ private:
         GB_CUDA(cudaGetLastError());
     }
 
-    CsrDev<T> csrA() const { return csr(planA_, A_val_.as<T>()); }
-    CsrDev<T> csrPAt() const { return csr(planPAt_, PAt_val_.as<T>()); }
+    CsrDev<T> csrA(int grid) const { return csr(planA_, A_val_.as<T>(), grid); }
+    CsrDev<T> csrPAt(int grid) const { return csr(planPAt_, PAt_val_.as<T>(), grid); }
 
     Vecs<T> vecs() const {
         Vecs<T> v;
@@ -1398,10 +1461,9 @@ private:
         v.diagp = diagp_.as<T>();
         v.colsq = colsq_.as<T>();
         v.rs = s_.rho_vector ? rs_.as<T>() : nullptr;
-        v.pc = pc_.as<T>();
+        v.ypc = ypc_.as<pair_t<T>>();
         v.kp = kp_.as<T>();
         v.r = r_.as<T>();
-        v.yv = yv_.as<T>();
         v.D = D_.as<double>();
         v.E = E_.as<double>();
         v.Dinv = Dinv_.as<double>();
@@ -1422,7 +1484,7 @@ private:
 
     void spmv_dev(const DevPlan &pl, const T *val, const T *x, T *y, T alpha) {
         const int g = grid_for_items(pl.nitems, (const void *)k_spmv<T, T>, kSmemT);
-        launch_smem(k_spmv<T, T>, g, kThreads, kSmemT, stream_, csr(pl, val), x, y, alpha);
+        launch_smem(k_spmv<T, T>, g, kThreads, kSmemT, stream_, csr(pl, val, g), x, y, alpha);
         GB_CUDA(cudaGetLastError());
     }
     void k_spmv_d(CsrDev<T> M, const T *x, double *y, int g) {
@@ -1432,26 +1494,26 @@ private:
 
     // ---- host-driven launches (same kernels as the graph)
     void launch_init(const Vecs<T> &v, Status *st, cudaGraphConditionalHandle h, int use_h) {
-        launch_smem(k_pcg_init<T>, gInit_, kThreads, kSmemT, stream_, csrPAt(), v, st, partials_.as<double>(), h, use_h);
+        launch_smem(k_pcg_init<T>, gInit_, kThreads, kSmemT, stream_, csrPAt(gInit_), v, st, partials_.as<double>(), h, use_h);
         GB_CUDA(cudaGetLastError());
     }
     void launch_step(const Vecs<T> &v, Status *st, cudaGraphConditionalHandle h, int use_h) {
-        launch_smem(k_pcg_p_t<T>, gPt_, kThreads, kSmemT, stream_, csrA(), v, st);
-        launch_smem(k_pcg_kp<T>, gKp_, kThreads, kSmemT, stream_, csrPAt(), v, st, partials_.as<double>());
+        launch_smem(k_pcg_p_t<T>, gPt_, kThreads, kSmemT, stream_, csrA(gPt_), v, st);
+        launch_smem(k_pcg_kp<T>, gKp_, kThreads, kSmemT, stream_, csrPAt(gKp_), v, st, partials_.as<double>());
         launch(k_pcg_update<T>, gridVec_, kThreads, stream_, v, st, partials_.as<double>(), h, use_h);
         GB_CUDA(cudaGetLastError());
     }
     void launch_admm(const Vecs<T> &v, Status *st) {
-        launch_smem(k_admm_update<T>, gAdmm_, kThreads, kSmemT, stream_, csrA(), v, st);
+        launch_smem(k_admm_update<T>, gAdmm_, kThreads, kSmemT, stream_, csrA(gAdmm_), v, st);
         GB_CUDA(cudaGetLastError());
     }
     void launch_check(const Vecs<T> &v, Status *st, cudaGraphConditionalHandle h, int use_h) {
-        launch_smem(k_check_a<T>, gCa_, kThreads, kSmemD, stream_, csrA(), v, st, partials_.as<double>());
+        launch_smem(k_check_a<T>, gCa_, kThreads, kSmemD, stream_, csrA(gCa_), v, st, partials_.as<double>());
         if (inf_on_) {
-            launch_smem(k_inf_a<T>, gIa_, kThreads, kSmemT, stream_, csrA(), v, st, partials_.as<double>());
-            launch_smem(k_inf_b<T>, gIb_, kThreads, kSmemT, stream_, csrPAt(), v, st, partials_.as<double>());
+            launch_smem(k_inf_a<T>, gIa_, kThreads, kSmemT, stream_, csrA(gIa_), v, st, partials_.as<double>());
+            launch_smem(k_inf_b<T>, gIb_, kThreads, kSmemT, stream_, csrPAt(gIb_), v, st, partials_.as<double>());
         }
-        launch_smem(k_check_b<T>, gCb_, kThreads, kSmemD, stream_, csrPAt(), v, st, partials_.as<double>(), policy(), h, use_h);
+        launch_smem(k_check_b<T>, gCb_, kThreads, kSmemD, stream_, csrPAt(gCb_), v, st, partials_.as<double>(), policy(), h, use_h);
         GB_CUDA(cudaGetLastError());
     }
     void launch_rho(const Vecs<T> &v, Status *st) {
@@ -1485,7 +1547,7 @@ private:
         Vecs<T> v = vecs();
         Status *st = st_.as<Status>();
         double *part = partials_.as<double>();
-        CsrDev<T> A = csrA(), PAt = csrPAt();
+
         GB_CUDA(cudaGraphCreate(&graph_, 0));
         cudaGraphConditionalHandle hA;
         GB_CUDA(cudaGraphConditionalHandleCreate(&hA, graph_, 1, cudaGraphCondAssignDefault));
@@ -1497,20 +1559,20 @@ private:
         for (int s = 0; s < s_.check_every; ++s) {
             cudaGraphConditionalHandle hP;
             GB_CUDA(cudaGraphConditionalHandleCreate(&hP, body, 0, 0));
-            cudaGraphNode_t ni = add_kernel_smem(body, prev ? &prev : nullptr, k_pcg_init<T>, gInit_, kSmemT, PAt, v, st, part, hP, 1);
+            cudaGraphNode_t ni = add_kernel_smem(body, prev ? &prev : nullptr, k_pcg_init<T>, gInit_, kSmemT, csrPAt(gInit_), v, st, part, hP, 1);
             cudaGraph_t pbody;
             cudaGraphNode_t nw = add_while(body, &ni, hP, &pbody);
-            cudaGraphNode_t a = add_kernel_smem(pbody, nullptr, k_pcg_p_t<T>, gPt_, kSmemT, A, v, (const Status *)st);
-            cudaGraphNode_t b = add_kernel_smem(pbody, &a, k_pcg_kp<T>, gKp_, kSmemT, PAt, v, st, part);
+            cudaGraphNode_t a = add_kernel_smem(pbody, nullptr, k_pcg_p_t<T>, gPt_, kSmemT, csrA(gPt_), v, (const Status *)st);
+            cudaGraphNode_t b = add_kernel_smem(pbody, &a, k_pcg_kp<T>, gKp_, kSmemT, csrPAt(gKp_), v, st, part);
             add_kernel(pbody, &b, k_pcg_update<T>, gridVec_, v, st, part, hP, 1);
-            prev = add_kernel_smem(body, &nw, k_admm_update<T>, gAdmm_, kSmemT, A, v, st);
+            prev = add_kernel_smem(body, &nw, k_admm_update<T>, gAdmm_, kSmemT, csrA(gAdmm_), v, st);
         }
-        cudaGraphNode_t ca = add_kernel_smem(body, &prev, k_check_a<T>, gCa_, kSmemD, A, v, st, part);
+        cudaGraphNode_t ca = add_kernel_smem(body, &prev, k_check_a<T>, gCa_, kSmemD, csrA(gCa_), v, st, part);
         if (inf_on_) {
-            ca = add_kernel_smem(body, &ca, k_inf_a<T>, gIa_, kSmemT, A, v, st, part);
-            ca = add_kernel_smem(body, &ca, k_inf_b<T>, gIb_, kSmemT, PAt, v, st, part);
+            ca = add_kernel_smem(body, &ca, k_inf_a<T>, gIa_, kSmemT, csrA(gIa_), v, st, part);
+            ca = add_kernel_smem(body, &ca, k_inf_b<T>, gIb_, kSmemT, csrPAt(gIb_), v, st, part);
         }
-        cudaGraphNode_t cb = add_kernel_smem(body, &ca, k_check_b<T>, gCb_, kSmemD, PAt, v, st, part, policy(), hA, 1);
+        cudaGraphNode_t cb = add_kernel_smem(body, &ca, k_check_b<T>, gCb_, kSmemD, csrPAt(gCb_), v, st, part, policy(), hA, 1);
         add_kernel(body, &cb, k_rho_apply<T>, gridN_, v, (const Status *)st);
         GB_CUDA(cudaGraphInstantiate(&exec_, graph_, 0));
     }
@@ -1550,7 +1612,7 @@ private:
     DevBuf A_rowptr_, A_col_, A_val_, PAt_rowptr_, PAt_col_, PAt_val_, PAt_pend_;
     DevBuf D_, E_, Dinv_, Einv_;
     DevBuf dxy_, rs_;
-    DevBuf xy_, xt_, pt_, z_, zt_, l_, u_, q_, minv_, diagp_, colsq_, pc_, kp_, r_, yv_, tmp_n_, tmp_nm_;
+    DevBuf xy_, xt_, pt_, z_, zt_, l_, u_, q_, minv_, diagp_, colsq_, kp_, r_, ypc_, tmp_n_, tmp_nm_;
     DevBuf x_out_, y_out_, z_out_;
     DevBuf partials_, st_, st2_, policy_;
     DevPlan planA_, planPAt_;

@@ -52,6 +52,9 @@ public:
     virtual void check(double *out) = 0;
     virtual double bench_kernel(int kernel, int reps) = 0;
     virtual void set_lambda(double lambda, double eps) = 0;
+    // the next solve continues from the current iterates, rho, PCG tolerance
+    // and lambda (iteration count from 0)
+    virtual void resume() = 0;
     // y = M x on device arrays of the working precision, with the long-row
     // scratch supplied by the caller (part: 2 doubles per work item, count:
     // one int per long row); allocates nothing.

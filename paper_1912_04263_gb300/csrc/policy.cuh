@@ -1,9 +1,11 @@
 // rho adaptation on the device: the residual-ratio rule (paper Section 3.4,
 // applied every rho_every iterations as in Section 5.3.3) and the learned
 // policy, a 4-64-64-2 MLP with BF16 operands and FP32 accumulation that
-// proposes a log-rho multiplier (and optionally a log factor on the PCG
-// tolerance weight lambda of Section 5.3.4).  The learned policy is not part
-// of the paper; it falls back to the ratio rule whenever progress stalls.
+// proposes rho as a log correction to the ratio rule's proposal (and
+// optionally a log factor on the PCG tolerance weight lambda of Section
+// 5.3.4).  The learned policy is not part of the paper; a zero output
+// reproduces the ratio rule, and it falls back to the ratio rule whenever
+// progress stalls.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -35,7 +37,7 @@ __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__floa
 // Residual-ratio rule (reading S2): rho * sqrt((||r_p|| / max(||Ax||, ||z||)) /
 // (||r_d|| / max(||Px||, ||A'y||, ||q||))) on scaled quantities, clamped;
 // a zero normaliser or dual residual leaves rho unchanged.
-__device__ __forceinline__ double rho_ratio(const Status *st) {
+__host__ __device__ __forceinline__ double rho_ratio(const Status *st) {
     const double prim_norm = fmax(st->ax_s, st->z_s);
     const double dual_norm = fmax(fmax(st->px_s, st->aty_s), st->qnorm_s);
     if (!(prim_norm > 0.0) || !(dual_norm > 0.0) || !(st->rd_s > 0.0)) return st->rho;
@@ -111,7 +113,7 @@ __device__ __forceinline__ void policy_decide(const PolicyDev &pol, Status *st, 
         if (use && isfinite(out[0]) && isfinite(out[1])) {
             const float cl = P[kOffExtra + 0];
             const float lm = fminf(fmaxf(out[0], -cl), cl);
-            nr = fmin(fmax(st->rho * exp((double)lm), st->rho_min), st->rho_max);
+            nr = fmin(fmax(rho_ratio(st) * exp((double)lm), st->rho_min), st->rho_max);
             if (P[kOffExtra + 3] != 0.f) {
                 const double lam = 0.15 * exp((double)out[1]);
                 st->lambda = fmin(fmax(lam, (double)P[kOffExtra + 1]), (double)P[kOffExtra + 2]);

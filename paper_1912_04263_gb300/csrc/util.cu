@@ -100,4 +100,33 @@ HostPlan build_plan(const std::vector<int> &rp) {
     return hp;
 }
 
+HostPartition partition_items(const HostPlan &hp, int grid) {
+    HostPartition out;
+    const int n = (int)hp.items.size();
+    grid = std::max(1, std::min(grid, std::max(n, 1)));
+    std::vector<long long> prefix(n + 1, 0);
+    for (int i = 0; i < n; ++i)
+        prefix[i + 1] = prefix[i] + (long long)(hp.items[i].k1 - hp.items[i].k0) + kItemCost;
+    out.part.assign(grid + 1, 0);
+    out.part[grid] = n;
+    for (int b = 1; b < grid; ++b) {
+        const long long target = (long long)((double)prefix[n] * b / grid);
+        int j = (int)(std::lower_bound(prefix.begin(), prefix.end(), target) - prefix.begin());
+        if (j > 0 && target - prefix[j - 1] < prefix[j] - target) --j;  // nearer boundary
+        // strictly increasing, leaving one item for each remaining CTA
+        j = std::max(j, out.part[b - 1] + 1);
+        j = std::min(j, n - (grid - b));
+        out.part[b] = j;
+    }
+    out.lr_cta.resize(hp.longrows.size());
+    auto cta_of = [&](int item) {
+        return (int)(std::upper_bound(out.part.begin(), out.part.end(), item) - out.part.begin()) - 1;
+    };
+    for (size_t l = 0; l < hp.longrows.size(); ++l) {
+        const LongRow &L = hp.longrows[l];
+        out.lr_cta[l] = make_int2(cta_of(L.first_item), cta_of(L.first_item + L.npieces - 1));
+    }
+    return out;
+}
+
 }  // namespace gb

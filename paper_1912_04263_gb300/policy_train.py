@@ -3,16 +3,18 @@ generates itself, on the GPU, and evaluate it on held-out QPs.
 
 The policy is not part of the paper.  Training problems mix the random,
 Lasso and portfolio families (seeds disjoint from every evaluation seed).
-Labels come from a short lookahead at
-every rho decision (every 10 ADMM iterations): from the current state the
-solver runs H iterations for each candidate (rho multiplier, lambda) pair,
-and the label is the candidate with the largest progress per unit of work,
-    (log merit_0 - log max(merit_H, 1)) / (PCG steps + 2 x iterations),
-with merit = max(r_prim / eps_prim, r_dual / eps_dual) (merit <= 1 means
-solved).  The trajectory then continues from that candidate's end state.
+Labels come from rollouts at every rho
+decision (every 10 ADMM iterations): from the current state each candidate
+(rho, lambda) pair, rho being the residual-ratio rule's proposal times a
+multiplier, is held for 10 iterations, after which the ratio rule decides
+until the solve ends (one CUDA-graph solve per rollout); the label is the
+candidate with the least remaining work, PCG steps + 2 x ADMM iterations
+(one step of policy improvement over the ratio rule).  The trajectory then
+continues with the chosen candidate.
 Features: log ||r_prim||, log ||r_dual|| (scaled problem), log rho,
-log(1 + PCG steps in the last 10 iterations).  Targets: the chosen log rho
-multiplier and log(lambda / 0.15).
+log(1 + PCG steps in the last 10 iterations).  Targets: the chosen log
+multiplier of the ratio rule's rho (0: follow the rule) and
+log(lambda / 0.15).
 
 Training runs on the device through the library's BF16 kernels (Adam, FP32
 master weights); the weights are written with binding.save_policy.  The
@@ -40,17 +42,13 @@ if ROOT not in sys.path:
 import qpgen  # noqa: E402
 from paper_1912_04263_gb300 import binding as gb  # noqa: E402
 
-LOG_MULTS = [-math.log(10.0), -math.log(3.0), 0.0, math.log(3.0), math.log(10.0)]
-LAMBDAS = [0.05, 0.15, 0.5]
+# candidates, the ratio rule's own choice first so that ties keep it
+LOG_MULTS = [0.0, -math.log(3.0), math.log(3.0), -math.log(10.0), math.log(10.0)]
+LAMBDAS = [0.15, 0.05, 0.5]
 LAMBDA0 = 0.15
 EPS_MIN = 1e-7
-HORIZON = 10
 TRAIN_SEED0 = 100000
 EVAL_SEED0 = 200000
-
-
-def merit(c: dict) -> float:
-    return max(c["r_prim"] / c["eps_prim"], c["r_dual"] / c["eps_dual"])
 
 
 def features(c: dict, rho: float, pcg_steps: int) -> list:
@@ -62,12 +60,18 @@ def pcg_eps(c: dict, lam: float) -> float:
     return max(lam * math.sqrt(max(c["r_prim_s"], 0.0) * max(c["r_dual_s"], 0.0)), EPS_MIN)
 
 
-def trajectory(qp, max_decisions: int = 60):
-    """Lookahead-labelled decision points of one solve (FP32)."""
+def trajectory(qp, max_decisions: int = 40, rollout_iters: int = 2000):
+    """Decision points of one FP32 solve, each labelled by rollouts: from the
+    current state, every candidate (rho, lambda) is held for the next 10
+    iterations and the ratio rule decides after that, until the solve ends;
+    the label is the candidate with the least remaining work (PCG steps + 2 x
+    iterations), ties to the ratio rule's own choice.  The trajectory then
+    continues with the chosen candidate."""
     s = gb.Solver(qp, precision=gb.FP32, loop_mode=gb.LOOP_HOST, rho_policy=gb.RHO_FIXED)
-    h = s.h
+    ro = gb.Solver(qp, precision=gb.FP32, rho_policy=gb.RHO_RATIO, max_iter=rollout_iters)
+    h, hr = s.h, ro.h
     n, m = s.n, s.m
-    rho, lam = 0.1, LAMBDA0
+    rho = 0.1
     gb.gbosqp_set_iterates(h, np.zeros(n), np.zeros(m), np.zeros(m), np.zeros(n), rho)
     st, per = gb.gbosqp_admm_iterations(h, 10)
     samples = []
@@ -75,30 +79,29 @@ def trajectory(qp, max_decisions: int = 60):
         if st != 0:
             break
         c0 = gb.gbosqp_check(h)
-        m0 = merit(c0)
         f = features(c0, rho, int(per.sum()))
+        rho_r = c0["rho_ratio"]
         x, z, y, xt, _ = gb.gbosqp_get_iterates(h)
         best = None
         for lm in LOG_MULTS:
             for lc in LAMBDAS:
-                r = min(max(rho * math.exp(lm), 1e-6), 1e6)
-                gb.gbosqp_set_iterates(h, x, z, y, xt, r)
-                gb.gbosqp_set_pcg_lambda(h, lc, pcg_eps(c0, lc))
-                st2, per2 = gb.gbosqp_admm_iterations(h, HORIZON)
-                iters = gb.osqp_get_info(h)["iters"]
-                mH = merit(gb.gbosqp_check(h))
-                progress = math.log(m0) - math.log(max(mH, 1.0)) if math.isfinite(mH) else -1e9
-                rate = progress / (float(per2.sum()) + 2.0 * iters)
-                if best is None or rate > best[0]:
-                    best = (rate, lm, lc, r, st2, per2.copy(), gb.gbosqp_get_iterates(h))
-        _, lm, lc, r, st, per, state = best
+                r = min(max(rho_r * math.exp(lm), 1e-6), 1e6)
+                gb.gbosqp_set_iterates(hr, x, z, y, xt, r)
+                gb.gbosqp_set_pcg_lambda(hr, lc, pcg_eps(c0, lc))
+                gb.gbosqp_resume(hr)
+                st_r = gb.osqp_solve(hr)
+                info = gb.osqp_get_info(hr)
+                work = float(info["pcg_iters"] + 2 * info["iters"]) if st_r == gb.SOLVED else math.inf
+                if best is None or work < best[0]:
+                    best = (work, lm, lc, r)
+        _, lm, lc, r = best
         samples.append(f + [lm, math.log(lc / LAMBDA0)])
-        rho, lam = r, lc
-        xb, zb, yb, xtb, _ = state
-        gb.gbosqp_set_iterates(h, xb, zb, yb, xtb, rho)
-        c1 = gb.gbosqp_check(h)
-        gb.gbosqp_set_pcg_lambda(h, lam, pcg_eps(c1, lam))
+        rho = r
+        gb.gbosqp_set_iterates(h, x, z, y, xt, rho)
+        gb.gbosqp_set_pcg_lambda(h, lc, pcg_eps(c0, lc))
+        st, per = gb.gbosqp_admm_iterations(h, 10)
     s.close()
+    ro.close()
     return samples
 
 
@@ -200,19 +203,25 @@ def eval_problems(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "policy"))
-    ap.add_argument("--train", type=int, default=240, help="training trajectories")
+    ap.add_argument("--train", type=int, default=400, help="training trajectories")
     ap.add_argument("--eval", type=int, default=24, help="held-out problems at n = --eval-n")
     ap.add_argument("--eval-n", type=int, default=3000)
     ap.add_argument("--eval-large", type=int, default=4, help="held-out problems at n = 5000")
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--eval-family", type=int, default=6, help="held-out Lasso and portfolio problems each")
     ap.add_argument("--eval-full", action="store_true", help="also the full-size Lasso, portfolio, random QPs")
+    ap.add_argument("--max-seconds", type=float, default=1e9, help="stop generating trajectories after this time")
     args = ap.parse_args()
     os.makedirs(args.out, exist_ok=True)
     t0 = time.time()
     rng = np.random.default_rng(12345)
     samples = []
+    done = 0
     for i in range(args.train):
+        if time.time() - t0 > args.max_seconds:
+            print(f"time budget reached after {i} trajectories", flush=True)
+            break
+        done += 1
         name, qp = training_problem(i, rng)
         samples.extend(trajectory(qp))
         if i % 20 == 0:
@@ -229,7 +238,7 @@ def main():
         sub = [r for r in rows if r["problem"].startswith(fam)]
         if sub:
             summary["family_" + fam] = summarize(sub)
-    report = {"train_trajectories": int(args.train),
+    report = {"train_trajectories": int(done),
               "train_families": "random n in [500, 2500] (half), Lasso f in [50, 400] x 20f, portfolio "
                                 "[2000, 10000] assets x [20, 100] factors",
               "samples": int(len(S)), "loss_first": float(hist[:50].mean()), "loss_last": float(hist[-50:].mean()),
