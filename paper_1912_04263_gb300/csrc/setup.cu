@@ -2,13 +2,17 @@
 // Section 5.4 "Matrix Equilibration"):
 //   1. validation of the CSR inputs and bounds (device kernels, one flag word)
 //   2. A' in CSR by a stable LSD radix sort of A's nonzeros by column
-//      (so every row of A' is sorted), and the full P from its upper
-//      triangle as U'(strictly lower part) followed by U, row by row
+//      (so every row of A' is sorted; its row pointer comes from the sorted
+//      keys), and the full P from its upper triangle as U'(strictly lower
+//      part) followed by U, row by row
 //   3. Ruiz equilibration, Algorithm 2, in FP64: column inf-norms of
-//      M = [[P, A'], [A, 0]] as row norms of P, A' and A (a segmented max
-//      over CSR rows, Section 5.4.1), the scaling delta = 1/sqrt(norm),
-//      pre- and post-multiplication of P, A and A' by diagonal matrices
-//      (Sections 5.4.2-5.4.3), and the cost scaling gamma
+//      M_bar = [[P_bar, A_bar'], [A_bar, 0]] as row norms of P, A' and A (a
+//      segmented max over CSR rows, Section 5.4.1) with the scaling so far
+//      applied on the fly (P_bar = c D P D, A_bar = E A D), the scaling
+//      delta = 1/sqrt(norm) accumulated into D and E, and the cost scaling
+//      gamma accumulated into c; the pre- and post-multiplication of P, A
+//      and A' by the diagonal matrices (Sections 5.4.2-5.4.3) is done once,
+//      after the last pass, instead of once per pass
 //   4. the concatenated [P_bar A_bar'] (row i: row i of P_bar, then row i
 //      of A_bar' with columns offset by n), diag(P_bar) and the squared
 //      column norms of A_bar for the Jacobi preconditioner (Section 5.3.1)
@@ -233,8 +237,10 @@ __global__ void k_radix_scatter(const int *kin, const int *vin, long long nnz, i
 }
 
 // Stable sort of (key, index) pairs by key (0 <= key <= max_key); returns
-// in perm the original positions in key order.
-void stable_sort_by_key(const int *keys, long long nnz, int max_key, int *perm, cudaStream_t st) {
+// in perm the original positions in key order and, if sorted is not null,
+// the keys in order.
+void stable_sort_by_key(const int *keys, long long nnz, int max_key, int *perm, cudaStream_t st,
+                        int *sorted = nullptr) {
     if (nnz == 0) return;
     Tmp ka(nnz * sizeof(int), st), kb(nnz * sizeof(int), st), va(nnz * sizeof(int), st),
         vb(nnz * sizeof(int), st);
@@ -256,6 +262,7 @@ void stable_sort_by_key(const int *keys, long long nnz, int max_key, int *perm, 
         shift += 8;
     } while (shift < 31 && (max_key >> shift) > 0);
     GB_CUDA(cudaMemcpyAsync(perm, vin, nnz * sizeof(int), cudaMemcpyDeviceToDevice, st));
+    if (sorted) GB_CUDA(cudaMemcpyAsync(sorted, kin, nnz * sizeof(int), cudaMemcpyDeviceToDevice, st));
 }
 
 // --------------------------------------------------------------- transpose
@@ -267,9 +274,15 @@ __global__ void k_expand_rows(const int *rp, int nrows, int *rowidx) {
     for (int k = rp[row] + lane; k < rp[row + 1]; k += 32) rowidx[k] = row;
 }
 
-__global__ void k_count_cols(const int *col, long long nnz, int *cnt) {
-    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < nnz) atomicAdd(cnt + col[k], 1);
+// Row pointer of the transpose from the sorted column keys: position k is
+// where every column strictly after key[k-1] and up to key[k] starts
+// (key[-1] = -1, key[nnz] = ncols).
+__global__ void k_col_bounds(const int *key, long long nnz, int ncols, int *rp) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > nnz) return;
+    const int c_prev = k == 0 ? -1 : key[k - 1];
+    const int c_cur = k == nnz ? ncols : key[k];
+    for (int c = c_prev + 1; c <= c_cur; ++c) rp[c] = (int)k;
 }
 
 __global__ void k_gather_t(const int *perm, const int *rowidx, const double *val, long long nnz, int *tcol,
@@ -299,14 +312,12 @@ Csr transpose(const int *rp, const int *col, const double *val, int nrows, int n
     T.rp.alloc((size_t)(ncols + 1) * sizeof(int));
     T.col.alloc(std::max<long long>(nnz, 1) * sizeof(int));
     T.val.alloc(std::max<long long>(nnz, 1) * sizeof(double));
-    Tmp cnt((size_t)std::max(ncols, 1) * sizeof(int), st);
-    GB_CUDA(cudaMemsetAsync(cnt.p, 0, (size_t)std::max(ncols, 1) * sizeof(int), st));
-    if (nnz > 0) launch(k_count_cols, blocks_for(nnz, 256), 256, st, col, nnz, cnt.as<int>());
-    exclusive_scan(cnt.as<int>(), ncols, T.rp.as<int>(), st);
+    if (nnz == 0) GB_CUDA(cudaMemsetAsync(T.rp.p, 0, (size_t)(ncols + 1) * sizeof(int), st));
     if (nnz > 0) {
-        Tmp rowidx(nnz * sizeof(int), st), perm(nnz * sizeof(int), st);
+        Tmp rowidx(nnz * sizeof(int), st), perm(nnz * sizeof(int), st), skey(nnz * sizeof(int), st);
         launch(k_expand_rows, warp_blocks(nrows), kThreads, st, rp, nrows, rowidx.as<int>());
-        stable_sort_by_key(col, nnz, std::max(ncols - 1, 0), perm.as<int>(), st);
+        stable_sort_by_key(col, nnz, std::max(ncols - 1, 0), perm.as<int>(), st, skey.as<int>());
+        launch(k_col_bounds, blocks_for(nnz + 1, 256), 256, st, (const int *)skey.as<int>(), nnz, ncols, T.rp.as<int>());
         launch(k_gather_t, blocks_for(nnz, 256), 256, st, perm.as<int>(), rowidx.as<int>(), val, nnz,
                                                          T.col.as<int>(), T.val.as<double>());
     }
@@ -353,19 +364,44 @@ __device__ __forceinline__ double limit_scaling(double v) {
     return v < 1e-4 ? 1.0 : (v > 1e4 ? 1e4 : v);
 }
 
-// out[r] = max(max|M1 row r|, max|M2 row r|) (M2 optional), one warp per row.
-__global__ void k_rownorm(const int *rp1, const double *v1, const int *rp2, const double *v2, int nrows,
-                          double *out) {
-    const int r = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+// Norms of the equilibrated matrices from the unscaled ones and the scaling
+// so far (the matrices are scaled once, after the last pass).  Maxima of
+// non-negative values on their bit patterns (integer pipe).
+__device__ __forceinline__ double nmax(double a, double b) {
+    const long long x = __double_as_longlong(a), y = __double_as_longlong(b);
+    return __longlong_as_double(x > y ? x : y);
+}
+
+// Columns j < n of [[P_bar, A_bar'], [A_bar, 0]]: out[j] = D_j max(c max_k
+// |P_jk| D_k, max_i |A'_ji| E_i), one warp per j (rows of P and of A').
+__global__ void k_norm_x(const int *prp, const int *pcol, const double *pval, const int *arp, const int *acol,
+                         const double *aval, int n, const double *D, const double *E, const double *scal,
+                         double *out) {
+    const int j = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
-    if (r >= nrows) return;
-    double mx = 0.0;
-    for (int k = rp1[r] + lane; k < rp1[r + 1]; k += 32) mx = fmax(mx, fabs(v1[k]));
-    if (rp2)
-        for (int k = rp2[r] + lane; k < rp2[r + 1]; k += 32) mx = fmax(mx, fabs(v2[k]));
+    if (j >= n) return;
+    double mp = 0.0, ma = 0.0;
+    for (int k = prp[j] + lane; k < prp[j + 1]; k += 32) mp = nmax(mp, fabs(pval[k]) * D[pcol[k]]);
+    for (int k = arp[j] + lane; k < arp[j + 1]; k += 32) ma = nmax(ma, fabs(aval[k]) * E[acol[k]]);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
-    if (lane == 0) out[r] = mx;
+    for (int o = 16; o > 0; o >>= 1) {
+        mp = nmax(mp, __shfl_down_sync(0xffffffffu, mp, o));
+        ma = nmax(ma, __shfl_down_sync(0xffffffffu, ma, o));
+    }
+    if (lane == 0) out[j] = D[j] * nmax(scal[0] * mp, ma);
+}
+
+// Columns n + i (rows of A_bar): out[i] = E_i max_j |A_ij| D_j.
+__global__ void k_norm_z(const int *rp, const int *col, const double *val, int m, const double *D, const double *E,
+                         double *out) {
+    const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= m) return;
+    double mx = 0.0;
+    for (int k = rp[i] + lane; k < rp[i + 1]; k += 32) mx = nmax(mx, fabs(val[k]) * D[col[k]]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = nmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    if (lane == 0) out[i] = E[i] * mx;
 }
 
 // delta = 1/sqrt(limit(norm)); accumulated scaling *= delta.
@@ -377,37 +413,41 @@ __global__ void k_delta(const double *norm, int n, double *delta, double *acc) {
     acc[i] *= d;
 }
 
-// M <- diag(rs) M diag(cs), one warp per row: v = (v * rs[r]) * cs[c].
+// M <- g diag(rs) M diag(cs), one warp per row: v = (v * (g rs[r])) * cs[c]
+// (g = *gp, or 1 when gp is null).
 __global__ void k_scale_csr(const int *rp, const int *col, double *val, int nrows, const double *rs,
-                            const double *cs) {
+                            const double *cs, const double *gp) {
     const int r = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (r >= nrows) return;
-    const double a = rs[r];
+    const double a = (gp ? *gp : 1.0) * rs[r];
     for (int k = rp[r] + lane; k < rp[r + 1]; k += 32) val[k] = (val[k] * a) * cs[col[k]];
 }
 
-__global__ void k_scale_vec(double *v, const double *s, int n) {
+// q_bar = c D q
+__global__ void k_scale_q_final(double *q, const double *D, const double *scal, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) v[i] = s[i] * v[i];
+    if (i < n) q[i] = (scal[0] * D[i]) * q[i];
 }
 
-// Cost scaling: gamma = 1 / limit(max(mean_j ||P_j||_inf, ||q||_inf)); c *= gamma.
+// Cost scaling: gamma = 1 / limit(max(mean_j ||P_bar_j||_inf, ||q_bar||_inf))
+// with P_bar = c D P D and q_bar = c D q after this pass's D; c *= gamma.
 // scal[0] = c, scal[1] = gamma.  Partial sums per CTA, last CTA finishes.
-__global__ void k_cost_scale(const int *prp, const double *pval, int n, const double *q, double *partials,
-                             unsigned int *ticket, double *scal) {
+__global__ void k_cost_scale(const int *prp, const int *pcol, const double *pval, int n, const double *q,
+                             const double *D, double *partials, unsigned int *ticket, double *scal) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double c = scal[0];
     double sum = 0.0, qmax = 0.0;
     const int nwarps_grid = gridDim.x * kWarps;
     for (int r = blockIdx.x * kWarps + warp; r < n; r += nwarps_grid) {
         double mx = 0.0;
-        for (int k = prp[r] + lane; k < prp[r + 1]; k += 32) mx = fmax(mx, fabs(pval[k]));
+        for (int k = prp[r] + lane; k < prp[r + 1]; k += 32) mx = nmax(mx, fabs(pval[k]) * D[pcol[k]]);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
-        if (lane == 0) sum += mx;
+        for (int o = 16; o > 0; o >>= 1) mx = nmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+        if (lane == 0) sum += c * D[r] * mx;
     }
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        qmax = fmax(qmax, fabs(q[i]));
+        qmax = nmax(qmax, fabs(c * D[i] * q[i]));
     Red<1, 1> red;
     red.s[0] = sum;
     red.m[0] = qmax;
@@ -420,11 +460,6 @@ __global__ void k_cost_scale(const int *prp, const double *pval, int n, const do
         }
     };
     grid_finish<1, 1>(red, partials, ticket, fin);
-}
-
-__global__ void k_scale_by(double *v, long long n, const double *g) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) v[i] *= *g;
 }
 
 __global__ void k_fill(double *v, long long n, double a) {
@@ -660,29 +695,32 @@ SetupData device_setup(const gbosqp_csr &P, const gbosqp_csr &A, const double *q
     launch(k_fill, blocks_for(m, 256), 256, st, sd.E.as<double>(), m, 1.0);
     launch(k_fill, 1, 32, st, scal.as<double>(), 1, 1.0);
     for (int pass = 0; pass < s.scaling_iters; ++pass) {
-        // column inf-norms of [[P, A'], [A, 0]]: columns j <= n are rows of
-        // P and A'; columns n + i are rows of A
-        if (n) launch(k_rownorm, warp_blocks(n), kThreads, st, Pf.rp.as<int>(), Pf.val.as<double>(), At.rp.as<int>(),
-                                                             At.val.as<double>(), n, nx.as<double>());
-        if (m) launch(k_rownorm, warp_blocks(m), kThreads, st, Ain.rp.as<int>(), Ain.val.as<double>(), nullptr, nullptr,
-                                                             m, nz.as<double>());
+        // column inf-norms of [[P_bar, A_bar'], [A_bar, 0]] from the unscaled
+        // matrices and the scaling so far: columns j < n are rows of P and
+        // A'; columns n + i are rows of A
+        if (n) launch(k_norm_x, warp_blocks(n), kThreads, st, Pf.rp.as<int>(), Pf.col.as<int>(), Pf.val.as<double>(),
+                                                            At.rp.as<int>(), At.col.as<int>(), At.val.as<double>(), n,
+                                                            sd.D.as<double>(), sd.E.as<double>(), scal.as<double>(),
+                                                            nx.as<double>());
+        if (m) launch(k_norm_z, warp_blocks(m), kThreads, st, Ain.rp.as<int>(), Ain.col.as<int>(), Ain.val.as<double>(),
+                                                            m, sd.D.as<double>(), sd.E.as<double>(), nz.as<double>());
         if (n) launch(k_delta, blocks_for(n, 256), 256, st, nx.as<double>(), n, dx.as<double>(), sd.D.as<double>());
         if (m) launch(k_delta, blocks_for(m, 256), 256, st, nz.as<double>(), m, dz.as<double>(), sd.E.as<double>());
-        // P <- dx P dx, A <- dz A dx, A' <- dx A' dz, q <- dx q
-        if (n) launch(k_scale_csr, warp_blocks(n), kThreads, st, Pf.rp.as<int>(), Pf.col.as<int>(), Pf.val.as<double>(),
-                                                               n, dx.as<double>(), dx.as<double>());
-        if (m) launch(k_scale_csr, warp_blocks(m), kThreads, st, Ain.rp.as<int>(), Ain.col.as<int>(),
-                                                               Ain.val.as<double>(), m, dz.as<double>(), dx.as<double>());
-        if (n) launch(k_scale_csr, warp_blocks(n), kThreads, st, At.rp.as<int>(), At.col.as<int>(), At.val.as<double>(),
-                                                               n, dx.as<double>(), dz.as<double>());
-        if (n) launch(k_scale_vec, blocks_for(n, 256), 256, st, sd.q.as<double>(), dx.as<double>(), n);
-        // cost scaling
-        launch(k_cost_scale, cs_grid, kThreads, st, Pf.rp.as<int>(), Pf.val.as<double>(), n, sd.q.as<double>(),
-                                                   partials.as<double>(), ticket.as<unsigned int>(), scal.as<double>());
-        if (Pf.nnz) launch(k_scale_by, blocks_for(Pf.nnz, 256), 256, st, Pf.val.as<double>(), Pf.nnz, scal.as<double>() + 1);
-        if (n) launch(k_scale_by, blocks_for(n, 256), 256, st, sd.q.as<double>(), n, scal.as<double>() + 1);
+        // cost scaling on P_bar = c D P D, q_bar = c D q with the new D
+        launch(k_cost_scale, cs_grid, kThreads, st, Pf.rp.as<int>(), Pf.col.as<int>(), Pf.val.as<double>(), n,
+                                                   sd.q.as<double>(), sd.D.as<double>(), partials.as<double>(),
+                                                   ticket.as<unsigned int>(), scal.as<double>());
         GB_CUDA(cudaGetLastError());
     }
+    // the scaled problem: P <- c D P D, A <- E A D, A' <- D A' E, q <- c D q
+    if (n) launch(k_scale_csr, warp_blocks(n), kThreads, st, Pf.rp.as<int>(), Pf.col.as<int>(), Pf.val.as<double>(), n,
+                                                           sd.D.as<double>(), sd.D.as<double>(), (const double *)scal.as<double>());
+    if (m) launch(k_scale_csr, warp_blocks(m), kThreads, st, Ain.rp.as<int>(), Ain.col.as<int>(), Ain.val.as<double>(), m,
+                                                           sd.E.as<double>(), sd.D.as<double>(), (const double *)nullptr);
+    if (n) launch(k_scale_csr, warp_blocks(n), kThreads, st, At.rp.as<int>(), At.col.as<int>(), At.val.as<double>(), n,
+                                                           sd.D.as<double>(), sd.E.as<double>(), (const double *)nullptr);
+    if (n) launch(k_scale_q_final, blocks_for(n, 256), 256, st, sd.q.as<double>(), (const double *)sd.D.as<double>(),
+                                                               (const double *)scal.as<double>(), n);
     if (m) launch(k_scale_bounds, blocks_for(m, 256), 256, st, sd.l.as<double>(), sd.u.as<double>(), sd.E.as<double>(), m);
     GB_CUDA(cudaMemcpyAsync(&sd.c, scal.p, sizeof(double), cudaMemcpyDeviceToHost, st));
 
