@@ -128,10 +128,13 @@ int osqp_setup(gbosqp_handle **out, const gbosqp_csr *P, const gbosqp_csr *A, co
     h->s = s;
     try {
         GB_CUDA(cudaSetDevice(s.device));
-        cudaDeviceProp prop;
-        GB_CUDA(cudaGetDeviceProperties(&prop, s.device));
-        if (prop.major * 10 + prop.minor != 103)
-            gb::fail(GBOSQP_ERR_UNSUPPORTED, std::string("device ") + prop.name + " is not sm_103 (this build targets sm_103a)");
+        int cc_major = 0, cc_minor = 0;
+        GB_CUDA(cudaDeviceGetAttribute(&cc_major, cudaDevAttrComputeCapabilityMajor, s.device));
+        GB_CUDA(cudaDeviceGetAttribute(&cc_minor, cudaDevAttrComputeCapabilityMinor, s.device));
+        if (cc_major * 10 + cc_minor != 103)
+            gb::fail(GBOSQP_ERR_UNSUPPORTED, "device " + std::to_string(s.device) + " has compute capability " +
+                                                 std::to_string(cc_major) + "." + std::to_string(cc_minor) +
+                                                 ", not 10.3 (this build targets sm_103a)");
         if (s.cuda_stream) {
             h->stream = (cudaStream_t)s.cuda_stream;
         } else {

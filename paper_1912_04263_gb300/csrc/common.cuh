@@ -418,11 +418,20 @@ __device__ __forceinline__ void reduce_rows(const CsrDev<T> &M, const Item &it, 
     }
 }
 
-// Dynamic shared memory of a row-block kernel (the products of one item,
-// kept in the working precision; rows accumulate them in Acc).
-template <class T, class Acc>
+// Whether a row-block kernel double-buffers its products and row sums (no
+// closing barrier per item).  Not for FP64 sums of split rows, whose row-sum
+// buffers are the largest and where the extra shared memory measured slower.
+template <class Acc, bool SPLIT>
+constexpr bool rowblock_double_buffered() {
+    return !(SPLIT && sizeof(Acc) == 8);
+}
+
+// Dynamic shared memory of a row-block kernel: the products of one item
+// (two when double-buffered), kept in the working precision; rows
+// accumulate them in Acc.
+template <class T, class Acc, bool SPLIT = false>
 constexpr size_t rowblock_smem() {
-    return (size_t)kCap * sizeof(T);
+    return (rowblock_double_buffered<Acc, SPLIT>() ? 2 : 1) * (size_t)kCap * sizeof(T);
 }
 
 // Load the value/column range of an item into registers (streaming loads:
@@ -502,9 +511,15 @@ __device__ __forceinline__ void finish_long_rows(const CsrDev<T> &M, int i0, int
 // column c in the accumulation type; epi.row(r, s1, s2, red) consumes rows.
 template <class Acc, bool SPLIT, class T, class Gather, class Epi, class RedT>
 __device__ __forceinline__ bool run_items(const CsrDev<T> &M, const Gather &gather, Epi &epi, RedT &red) {
+    // Products and row sums are double-buffered by item parity: item i+1
+    // writes the other buffers while slow threads may still read item i's, and
+    // the barrier after item i+1's products orders item i's reads before item
+    // i+2 reuses them, so an item needs no closing barrier.  Single-buffered
+    // kernels close every item with a barrier instead.
+    constexpr bool kDB = rowblock_double_buffered<Acc, SPLIT>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sprod = reinterpret_cast<T *>(smem_raw);
-    __shared__ Acc rsum[SPLIT ? 2 : 1][kThreads];
+    T *sprod_buf = reinterpret_cast<T *>(smem_raw);
+    __shared__ Acc rsum_buf[kDB ? 2 : 1][SPLIT ? 2 : 1][kThreads];
     __shared__ Acc qsum[kRowBatch][2][kWarps];
     __shared__ int qlr[kRowBatch];
     const int i0 = M.part[blockIdx.x];
@@ -530,6 +545,9 @@ __device__ __forceinline__ bool run_items(const CsrDev<T> &M, const Gather &gath
         }
         const int nnz = it.k1 - it.k0;
         if (it.r1 >= 0) {
+            const int buf = kDB ? ((itx - i0) & 1) : 0;
+            T *sprod = sprod_buf + buf * kCap;
+            Acc(*rsum)[kThreads] = rsum_buf[buf];
 #pragma unroll
             for (int u = 0; u < kPerThread; ++u) {
                 const int e = u * kThreads + threadIdx.x;
@@ -543,7 +561,7 @@ __device__ __forceinline__ bool run_items(const CsrDev<T> &M, const Gather &gath
             else if (avg >= 6) reduce_rows<8, SPLIT, Acc>(M, it, sprod, epi, red, rsum);
             else if (avg >= 3) reduce_rows<4, SPLIT, Acc>(M, it, sprod, epi, red, rsum);
             else reduce_rows<1, SPLIT, Acc>(M, it, sprod, epi, red, rsum);
-            __syncthreads();
+            if (!kDB) __syncthreads();
         } else {
             const int row = it.r0;
             const int sp = SPLIT ? __ldg(M.pend + row) - it.k0 : 0x7fffffff;

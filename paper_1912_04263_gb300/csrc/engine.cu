@@ -850,15 +850,17 @@ public:
                               (const void *)k_admm_update<T>, (const void *)k_spmv<T, T>, (const void *)k_inf_a<T>,
                               (const void *)k_inf_b<T>})
             GB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemT));
-        for (const void *k : {(const void *)k_check_a<T>, (const void *)k_check_b<T>, (const void *)k_spmv_dbl<T>})
+        for (const void *k : {(const void *)k_check_a<T>, (const void *)k_spmv_dbl<T>})
             GB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemD));
+        GB_CUDA(cudaFuncSetAttribute((const void *)k_check_b<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kSmemDS));
         // each kernel's grid: its items, capped at the CTAs that fit at once
         gPt_ = grid_for_items(planA_.nitems, (const void *)k_pcg_p_t<T>, kSmemT);
         gAdmm_ = grid_for_items(planA_.nitems, (const void *)k_admm_update<T>, kSmemT);
         gCa_ = grid_for_items(planA_.nitems, (const void *)k_check_a<T>, kSmemD);
         gKp_ = grid_for_items(planPAt_.nitems, (const void *)k_pcg_kp<T>, kSmemT);
         gInit_ = grid_for_items(planPAt_.nitems, (const void *)k_pcg_init<T>, kSmemT);
-        gCb_ = grid_for_items(planPAt_.nitems, (const void *)k_check_b<T>, kSmemD);
+        gCb_ = grid_for_items(planPAt_.nitems, (const void *)k_check_b<T>, kSmemDS);
         gIa_ = grid_for_items(planA_.nitems, (const void *)k_inf_a<T>, kSmemT);
         gIb_ = grid_for_items(planPAt_.nitems, (const void *)k_inf_b<T>, kSmemT);
         // vector kernels: about 4 elements per thread
@@ -1271,7 +1273,7 @@ public:
                 case GBOSQP_K_PCG_INIT: launch_smem(k_pcg_init<T>, gInit_, kThreads, kSmemT, stream_, csrPAt(gInit_), v, st, partials_.as<double>(), (cudaGraphConditionalHandle)0, 0); break;
                 case GBOSQP_K_ADMM_UPDATE: launch_smem(k_admm_update<T>, gAdmm_, kThreads, kSmemT, stream_, csrA(gAdmm_), v, st); break;
                 case GBOSQP_K_CHECK_A: launch_smem(k_check_a<T>, gCa_, kThreads, kSmemD, stream_, csrA(gCa_), v, st, partials_.as<double>()); break;
-                case GBOSQP_K_CHECK_B: launch_smem(k_check_b<T>, gCb_, kThreads, kSmemD, stream_, csrPAt(gCb_), v, st, partials_.as<double>(), policy(), (cudaGraphConditionalHandle)0, 0); break;
+                case GBOSQP_K_CHECK_B: launch_smem(k_check_b<T>, gCb_, kThreads, kSmemDS, stream_, csrPAt(gCb_), v, st, partials_.as<double>(), policy(), (cudaGraphConditionalHandle)0, 0); break;
                 case GBOSQP_K_INF_A: launch_smem(k_inf_a<T>, gIa_, kThreads, kSmemT, stream_, csrA(gIa_), v, st, partials_.as<double>()); break;
                 case GBOSQP_K_INF_B: launch_smem(k_inf_b<T>, gIb_, kThreads, kSmemT, stream_, csrPAt(gIb_), v, st, partials_.as<double>()); break;
                 default: fail(GBOSQP_ERR_INVALID_ARG, "unknown kernel selector");
@@ -1513,7 +1515,7 @@ private:
             launch_smem(k_inf_a<T>, gIa_, kThreads, kSmemT, stream_, csrA(gIa_), v, st, partials_.as<double>());
             launch_smem(k_inf_b<T>, gIb_, kThreads, kSmemT, stream_, csrPAt(gIb_), v, st, partials_.as<double>());
         }
-        launch_smem(k_check_b<T>, gCb_, kThreads, kSmemD, stream_, csrPAt(gCb_), v, st, partials_.as<double>(), policy(), h, use_h);
+        launch_smem(k_check_b<T>, gCb_, kThreads, kSmemDS, stream_, csrPAt(gCb_), v, st, partials_.as<double>(), policy(), h, use_h);
         GB_CUDA(cudaGetLastError());
     }
     void launch_rho(const Vecs<T> &v, Status *st) {
@@ -1572,7 +1574,7 @@ private:
             ca = add_kernel_smem(body, &ca, k_inf_a<T>, gIa_, kSmemT, csrA(gIa_), v, st, part);
             ca = add_kernel_smem(body, &ca, k_inf_b<T>, gIb_, kSmemT, csrPAt(gIb_), v, st, part);
         }
-        cudaGraphNode_t cb = add_kernel_smem(body, &ca, k_check_b<T>, gCb_, kSmemD, csrPAt(gCb_), v, st, part, policy(), hA, 1);
+        cudaGraphNode_t cb = add_kernel_smem(body, &ca, k_check_b<T>, gCb_, kSmemDS, csrPAt(gCb_), v, st, part, policy(), hA, 1);
         add_kernel(body, &cb, k_rho_apply<T>, gridN_, v, (const Status *)st);
         GB_CUDA(cudaGraphInstantiate(&exec_, graph_, 0));
     }
@@ -1620,6 +1622,7 @@ private:
     bool inf_on_ = false;
     static constexpr size_t kSmemT = rowblock_smem<T, T>();
     static constexpr size_t kSmemD = rowblock_smem<T, double>();
+    static constexpr size_t kSmemDS = rowblock_smem<T, double, true>();
     cudaGraph_t graph_ = nullptr;
     cudaGraphExec_t exec_ = nullptr;
     float solve_ms_ = 0.f;
