@@ -140,7 +140,11 @@ typedef struct {
                                                              default 0    */
     int32_t reserved1;
     void *cuda_stream;   /* cudaStream_t to run on; NULL: the library
-                            creates and owns one             default NULL */
+                            creates and owns one.  A caller's stream must
+                            stay valid until osqp_cleanup (the handle's
+                            device memory, taken from the device's
+                            stream-ordered pool, is returned on it)
+                                                             default NULL */
     const float *policy_params; /* learned policy parameters (host, FP32,
                                    GBOSQP_POLICY_PARAMS floats) or NULL    */
 } gbosqp_settings;

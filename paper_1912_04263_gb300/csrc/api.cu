@@ -2,6 +2,7 @@
 // point validates its arguments, runs the C++ implementation, and turns any
 // failure into a return code; no exception or abort crosses the boundary.
 #include <chrono>
+#include <mutex>
 #include <cmath>
 #include <memory>
 #include <string>
@@ -141,8 +142,21 @@ int osqp_setup(gbosqp_handle **out, const gbosqp_csr *P, const gbosqp_csr *A, co
             GB_CUDA(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
             h->own_stream = true;
         }
+        // device memory of the handle comes from the stream-ordered pool,
+        // which keeps freed memory for reuse by later set-ups of this process
+        static std::once_flag pool_once[64];
+        if (s.device >= 0 && s.device < 64)
+            std::call_once(pool_once[s.device], [&]() {
+                cudaMemPool_t pool;
+                if (cudaDeviceGetDefaultMemPool(&pool, s.device) == cudaSuccess) {
+                    uint64_t keep = ~0ULL;
+                    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+                }
+                cudaGetLastError();
+            });
         const auto t0 = std::chrono::steady_clock::now();
         const long long l0 = gb::g_launches;
+        gb::PoolScope pool_scope(h->stream);
         gb::SetupData sd = gb::device_setup(*P, *A, q, l, u, s, h->stream);
         h->eng = gb::make_engine(std::move(sd), s, h->stream);
         GB_CUDA(cudaStreamSynchronize(h->stream));

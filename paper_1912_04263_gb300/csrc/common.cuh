@@ -42,22 +42,50 @@ void check_cuda(cudaError_t e, const char *what, const char *file, int line);
 
 // ----------------------------------------------------------------- buffers
 
+// Device buffer.  Inside a PoolScope (osqp_setup) it comes from the
+// device's stream-ordered memory pool on the scope's stream and is returned
+// to the pool on that stream (no device-wide synchronisation, memory reused
+// by the next set-up); elsewhere it is a plain cudaMalloc allocation.
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
+    cudaStream_t pool_stream = nullptr;  // set when the buffer came from the pool
+    bool pooled = false;
     DevBuf() = default;
     explicit DevBuf(size_t nbytes) { alloc(nbytes); }
     DevBuf(const DevBuf &) = delete;
     DevBuf &operator=(const DevBuf &) = delete;
-    DevBuf(DevBuf &&o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+    DevBuf(DevBuf &&o) noexcept : p(o.p), bytes(o.bytes), pool_stream(o.pool_stream), pooled(o.pooled) {
+        o.p = nullptr;
+        o.bytes = 0;
+        o.pooled = false;
+    }
     DevBuf &operator=(DevBuf &&o) noexcept {
-        if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+        if (this != &o) {
+            release();
+            p = o.p;
+            bytes = o.bytes;
+            pool_stream = o.pool_stream;
+            pooled = o.pooled;
+            o.p = nullptr;
+            o.bytes = 0;
+            o.pooled = false;
+        }
         return *this;
     }
     ~DevBuf() { release(); }
     void alloc(size_t nbytes);
     void release();
     template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// Makes the DevBuf allocations of this host thread stream-ordered on s
+// while it lives (nested scopes restore the previous stream).  The stream
+// must outlive the buffers allocated in the scope.
+struct PoolScope {
+    cudaStream_t prev;
+    explicit PoolScope(cudaStream_t s);
+    ~PoolScope();
 };
 
 // -------------------------------------------------------------- constants

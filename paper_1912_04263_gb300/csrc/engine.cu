@@ -1371,11 +1371,10 @@ private:
 
     DevBuf convert(DevBuf &&src, long long count) {
         if (sizeof(T) == sizeof(double)) return std::move(src);
-        DevBuf out(sizeof(T) * (count + 8));  // bulk copies may read 3 past the end
+        DevBuf out(sizeof(T) * (count + 8));  // padding: vector loads may read past the end
         if (count) launch(k_from_double<T>, ceil_div(count, 256), 256, stream_, src.as<double>(), out.as<T>(), count);
         GB_CUDA(cudaGetLastError());
-        GB_CUDA(cudaStreamSynchronize(stream_));
-        return out;
+        return out;  // src is released after the conversion in stream order
     }
 
     void build_plan_dev(const std::vector<int> &rp, DevPlan &pl) {

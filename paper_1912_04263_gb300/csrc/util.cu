@@ -18,22 +18,50 @@ void check_cuda(cudaError_t e, const char *what, const char *file, int line) {
     throw GbError{code, std::string(what) + ": " + cudaGetErrorString(e) + " (" + file + ":" + std::to_string(line) + ")"};
 }
 
+namespace {
+thread_local cudaStream_t g_pool_stream = nullptr;
+thread_local bool g_pool_on = false;
+}  // namespace
+
+PoolScope::PoolScope(cudaStream_t s) : prev(g_pool_stream) {
+    g_pool_stream = s;
+    g_pool_on = true;
+}
+PoolScope::~PoolScope() {
+    g_pool_stream = prev;
+    g_pool_on = prev != nullptr;
+}
+
 void DevBuf::alloc(size_t nbytes) {
     release();
     if (nbytes == 0) nbytes = 16;
-    cudaError_t e = cudaMalloc(&p, nbytes);
+    cudaError_t e;
+    if (g_pool_on) {
+        e = cudaMallocAsync(&p, nbytes, g_pool_stream);
+        pooled = e == cudaSuccess;
+        pool_stream = g_pool_stream;
+    } else {
+        e = cudaMalloc(&p, nbytes);
+        pooled = false;
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         p = nullptr;
-        fail(GBOSQP_ERR_OOM, "cudaMalloc of " + std::to_string(nbytes) + " bytes failed: " + cudaGetErrorString(e));
+        pooled = false;
+        fail(GBOSQP_ERR_OOM, "device allocation of " + std::to_string(nbytes) + " bytes failed: " +
+                                 cudaGetErrorString(e));
     }
     bytes = nbytes;
 }
 
 void DevBuf::release() {
-    if (p) cudaFree(p);
+    if (p) {
+        if (pooled) cudaFreeAsync(p, pool_stream);
+        else cudaFree(p);
+    }
     p = nullptr;
     bytes = 0;
+    pooled = false;
 }
 
 int device_sm_count() {
