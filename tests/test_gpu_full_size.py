@@ -1,0 +1,115 @@
+"""Parity at the full sizes of the measured workloads, in the configuration
+the benchmark runs (FP32 with the trained rho policy, whole-solve CUDA
+graph): every solve is judged on the unscaled data in FP64 on the host by
+the optimality conditions (size-independent properties), sampled rows of
+the device SpMV are recomputed one by one, and on the Lasso workload (the
+benchmark's) the equilibration and the objective are compared with the
+oracle itself."""
+import functools
+import os
+
+import numpy as np
+import pytest
+
+import qpgen
+from oracle import admm, checks
+
+pytestmark = pytest.mark.gpu
+
+gb = pytest.importorskip("paper_1912_04263_gb300.binding")
+
+FULL = ["lasso_1000x100000", "random_20000x200000", "portfolio_100000x1000"]
+POLICY = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1912_04263_gb300",
+                      "policy", "rho_policy.bin")
+
+
+@functools.lru_cache(maxsize=None)
+def full(name):
+    return qpgen.by_name(name, 0)
+
+
+def bench_solver(qp):
+    """The benchmark's form: FP32, learned policy when the weights exist."""
+    kw = dict(precision=gb.FP32)
+    if os.path.exists(POLICY):
+        kw.update(rho_policy=gb.RHO_LEARNED, policy_params=gb.load_policy(POLICY))
+    return gb.Solver(qp, **kw)
+
+
+@pytest.mark.parametrize("name", FULL)
+def test_full_size_solution_meets_the_optimality_conditions(name):
+    qp = full(name)
+    with bench_solver(qp) as s:
+        st = s.solve()
+        x, y, z = s.solution()
+        info = s.info()
+    assert st == gb.SOLVED, info
+    v = checks.kkt_violation(qp, x, z, y)
+    assert v.prim <= info["eps_prim"] * (1 + 1e-6) + 1e-12, (v, info)
+    assert v.dual <= info["eps_dual"] * (1 + 1e-6) + 1e-12, (v, info)
+    assert v.box <= 1e-6 * max(1.0, float(np.max(np.abs(z))))
+    f = admm.objective(qp.P, qp.q, x)
+    assert abs(info["obj"] - f) <= 1e-6 * max(1.0, abs(f))
+
+
+@pytest.mark.parametrize("name", FULL)
+@pytest.mark.parametrize("which", ["A", "PAt"])
+def test_full_size_spmv_sampled_rows(name, which):
+    """Device SpMV (FP64 accumulation of FP32 products) of a random vector:
+    2000 sampled rows recomputed in FP64 from the device's own scaled CSR,
+    within the FP32 product rounding bound."""
+    qp = full(name)
+    with gb.Solver(qp, precision=gb.FP32) as s:
+        mat = gb.MAT_A if which == "A" else gb.MAT_PAT
+        M = gb.gbosqp_get_scaled_csr(s.h, mat)
+        rng = np.random.default_rng(3)
+        xv = rng.standard_normal(M.shape[1])
+        yd = gb.gbosqp_spmv(s.h, mat, xv, True)
+    x32 = xv.astype(np.float32).astype(np.float64)
+    rows = rng.choice(M.shape[0], size=min(2000, M.shape[0]), replace=False)
+    Ms = M[rows]
+    ref = Ms @ x32
+    bound = (np.diff(Ms.indptr) + 4) * 2.0 ** -24 * (abs(Ms) @ np.abs(x32)) + 1e-30
+    assert np.all(np.abs(yd[rows] - ref) <= bound)
+
+
+def test_lasso_full_size_equilibration_matches_oracle():
+    qp = full("lasso_1000x100000")
+    sc = admm.ruiz(qp.P, qp.q, qp.A, qp.l, qp.u, 10)
+    with gb.Solver(qp, precision=gb.FP32) as s:
+        D, E, c = gb.gbosqp_get_scaling(s.h)
+    rel = lambda a, b: float(np.max(np.abs(a - b)) / np.max(np.abs(b)))  # noqa: E731
+    assert rel(D, sc.D) <= 1e-12 and rel(E, sc.E) <= 1e-12 and abs(c - sc.c) <= 1e-12 * sc.c
+
+
+@pytest.mark.parametrize("form", ["learned_fp32", "plain_fp64"])
+def test_lasso_full_size_objective_matches_oracle(form):
+    """The benchmark's headline pair on its workload: both the learned FP32
+    form and the plain FP64 form reach the oracle's optimum within the
+    convexity bound of reading S15, and within 1e-3 relative if the oracle's
+    own 1e-3 solve gets there (the inf-norm stopping rule at 1e-3 does not
+    bound the objective error by 1e-3: on this instance 100000 equality rows
+    may each be violated by up to eps_prim)."""
+    qp = full("lasso_1000x100000")
+    ref = lasso_reference()
+    solver = bench_solver(qp) if form == "learned_fp32" else gb.Solver(qp, precision=gb.FP64)
+    with solver as s:
+        assert s.solve() == gb.SOLVED
+        x, y, z = s.solution()
+    v = checks.kkt_violation(qp, x, z, y)
+    f = admm.objective(qp.P, qp.q, x)
+    bound = checks.objective_error_bound(x, y, v.prim, v.dual, ref.x, ref.y)
+    assert abs(f - ref.obj) <= 1.001 * bound + 1e-9 * max(1.0, abs(ref.obj)), (f, ref.obj, bound)
+    own = lasso_oracle_1e3()
+    if abs(own.obj - ref.obj) <= 1e-3 * max(1.0, abs(ref.obj)):
+        assert abs(f - ref.obj) <= 1e-3 * max(1.0, abs(ref.obj)), (f, ref.obj, own.obj)
+
+
+@functools.lru_cache(maxsize=None)
+def lasso_reference():
+    return admm.solve(full("lasso_1000x100000"), admm.Settings(eps_abs=1e-6, eps_rel=1e-6, max_iter=20000))
+
+
+@functools.lru_cache(maxsize=None)
+def lasso_oracle_1e3():
+    return admm.solve(full("lasso_1000x100000"))
