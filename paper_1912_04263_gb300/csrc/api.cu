@@ -135,7 +135,7 @@ int osqp_setup(gbosqp_handle **out, const gbosqp_csr *P, const gbosqp_csr *A, co
         if (cc_major * 10 + cc_minor != 103)
             gb::fail(GBOSQP_ERR_UNSUPPORTED, "device " + std::to_string(s.device) + " has compute capability " +
                                                  std::to_string(cc_major) + "." + std::to_string(cc_minor) +
-                                                 ", not 10.3 (this build targets sm_103a)");
+                                                 ", not 10.3 (the library is compiled for sm_103a only)");
         if (s.cuda_stream) {
             h->stream = (cudaStream_t)s.cuda_stream;
         } else {
