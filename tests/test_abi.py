@@ -47,6 +47,21 @@ def test_default_settings_match_the_paper(lib):
     assert s.check_every == 5 and s.rho_every == 10
     assert s.pcg_lambda == 0.15 and s.pcg_eps_min == 1e-7
     assert s.rho0 == 0.1 and s.eps_abs == 1e-3 and s.eps_rel == 1e-3
+    # infeasibility tolerances of reading S17; the paper's R = rho I; cold starts
+    assert s.eps_prim_inf == 1e-4 and s.eps_dual_inf == 1e-4
+    assert s.rho_vector == 0 and s.warm_start == 0
+
+
+def test_settings_struct_layout_matches_the_header(lib):
+    """The ctypes mirror of gbosqp_settings has the header's field order (so
+    the binding and the C struct agree byte for byte)."""
+    from paper_1912_04263_gb300 import binding as gb
+    text = open(os.path.join(ROOT, "include", "gbosqp.h")).read()
+    body = text[text.index("typedef struct {\n    double alpha;"):]
+    body = body[:body.index("} gbosqp_settings;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"(?:double|int32_t|void\s*\*|const float\s*\*)\s*\**\s*(\w+)\s*;", body)
+    assert [f for f, _ in gb.Settings._fields_] == fields
 
 
 def test_error_strings_and_null_arguments(lib):
@@ -64,7 +79,9 @@ def test_settings_validation_is_host_side(lib):
     from paper_1912_04263_gb300 import binding as gb
     qp = qpgen.random_qp(5, 7, 0)
     for bad in [dict(alpha=2.0), dict(sigma=0.0), dict(check_every=0), dict(rho_every=7),
-                dict(precision=5), dict(rho_policy=gb.RHO_LEARNED)]:
+                dict(precision=5), dict(rho_policy=gb.RHO_LEARNED), dict(eps_prim_inf=-1e-4),
+                dict(eps_dual_inf=float("nan")), dict(eps_dual_inf=float("inf")), dict(warm_start=2),
+                dict(rho_vector=-1), dict(rho_min=0.0)]:
         with pytest.raises(gb.GbosqpError) as e:
             gb.Solver(qp, **bad)
         assert e.value.code == gb.ERR_INVALID_ARG, bad
