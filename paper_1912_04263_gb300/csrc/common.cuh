@@ -335,6 +335,34 @@ __device__ __forceinline__ Acc to_acc(T v) { return Acc(v); }
 template <>
 __device__ __forceinline__ double to_acc<double, float>(float v) { return f2d_exact(v); }
 
+// Per-lane running sum of products of type T in the accumulation type Acc.
+// For FP32 products summed in FP64 (the termination checks) a lane keeps a
+// compensated FP32 pair instead: Knuth's error-free TwoSum turns each
+// addition into a rounded sum and its exact rounding error, the errors are
+// summed separately, and the pair is converted to FP64 once (the summation
+// of Ogita, Rump and Oishi, "Accurate sum and dot product", 2005: as
+// accurate as summing in twice the working precision).  GB300's FP64 pipe is
+// narrow; this moves the per-product additions to the FP32 pipe while the
+// lane sums are still combined in FP64.
+template <class Acc, class T>
+struct LaneSum {
+    Acc s = Acc(0);
+    __device__ __forceinline__ void add(T x) { s += to_acc<Acc>(x); }
+    __device__ __forceinline__ Acc value() const { return s; }
+};
+template <>
+struct LaneSum<double, float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float t = __fadd_rn(s, x);
+        const float xp = __fsub_rn(t, s);
+        const float sp = __fsub_rn(t, xp);
+        c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, sp), __fsub_rn(x, xp)));
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return f2d_exact(s) + f2d_exact(c); }
+};
+
 // Row reduction of one block item with lane groups of G threads.  sprod
 // holds the item's products; epi.row(r, s1, s2, red) consumes each row.
 // With G = 1 every thread sums and finishes its own rows.  With G > 1 the
@@ -362,11 +390,9 @@ __device__ __forceinline__ void reduce_rows(const CsrDev<T> &M, const Item &it, 
     const bool transposed =
         kFp64 && nb <= kRounds && R * G * kParts * (int)sizeof(Acc) <= kCap * (int)sizeof(T);
     if (transposed) {
-        Acc p1[kRounds], p2[kRounds];
+        LaneSum<Acc, T> p1[kRounds], p2[kRounds];
 #pragma unroll
         for (int b = 0; b < kRounds; ++b) {
-            p1[b] = Acc(0);
-            p2[b] = Acc(0);
             const int lr = b * ngrp + grp;
             if (b < nb && lr < R) {
                 const int r = it.r0 + lr;
@@ -375,10 +401,10 @@ __device__ __forceinline__ void reduce_rows(const CsrDev<T> &M, const Item &it, 
                 if (SPLIT) {
                     const int sp = __ldg(M.pend + r) - it.k0;
                     for (int e = a + lane_g; e < e1; e += G) {
-                        if (e < sp) p1[b] += to_acc<Acc>(sprod[e]); else p2[b] += to_acc<Acc>(sprod[e]);
+                        if (e < sp) p1[b].add(sprod[e]); else p2[b].add(sprod[e]);
                     }
                 } else {
-                    for (int e = a + lane_g; e < e1; e += G) p1[b] += to_acc<Acc>(sprod[e]);
+                    for (int e = a + lane_g; e < e1; e += G) p1[b].add(sprod[e]);
                 }
             }
         }
@@ -388,8 +414,8 @@ __device__ __forceinline__ void reduce_rows(const CsrDev<T> &M, const Item &it, 
         for (int b = 0; b < kRounds; ++b) {
             const int lr = b * ngrp + grp;
             if (b < nb && lr < R) {
-                lp[lr * G + lane_g] = p1[b];
-                if (SPLIT) lp[R * G + lr * G + lane_g] = p2[b];
+                lp[lr * G + lane_g] = p1[b].value();
+                if (SPLIT) lp[R * G + lr * G + lane_g] = p2[b].value();
             }
         }
         __syncthreads();
@@ -561,7 +587,7 @@ __device__ __forceinline__ bool run_items(const CsrDev<T> &M, const Gather &gath
         load_item(M, cur, va, ca);
     }
     if (i0 + 1 < i1) nx = M.items[i0 + 1];
-    Acc ps1 = Acc(0), ps2 = Acc(0);  // running sums of a long row's pieces
+    LaneSum<Acc, T> ps1, ps2;  // running sums of a long row's pieces
     int nq = 0;                      // pending long-row ends (uniform in the CTA)
     for (int itx = i0; itx < i1; ++itx) {
         const Item it = cur;
@@ -597,15 +623,15 @@ __device__ __forceinline__ bool run_items(const CsrDev<T> &M, const Gather &gath
             for (int u = 0; u < kPerThread; ++u) {
                 const int e = u * kThreads + threadIdx.x;
                 if (e < nnz) {
-                    const Acc pr = to_acc<Acc>(va[u] * gather(ca[u]));
-                    if (!SPLIT || e < sp) ps1 += pr; else ps2 += pr;
+                    const T pr = va[u] * gather(ca[u]);
+                    if (!SPLIT || e < sp) ps1.add(pr); else ps2.add(pr);
                 }
             }
             const bool row_end = !has_next || nx.r1 != it.r1;
             if (row_end) {
-                Acc s1 = ps1, s2 = ps2;
-                ps1 = Acc(0);
-                ps2 = Acc(0);
+                Acc s1 = ps1.value(), s2 = ps2.value();
+                ps1 = LaneSum<Acc, T>();
+                ps2 = LaneSum<Acc, T>();
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
                     s1 += __shfl_down_sync(0xffffffffu, s1, o);
