@@ -201,14 +201,11 @@ enum Ticket { kTkI1 = 0, kTkK2, kTkK3, kTkC1, kTkC2, kTkSetupA, kTkSetupB, kTkSe
 
 // ------------------------------------------------------------- reductions
 
-__device__ __forceinline__ double nanmax(double a, double b) {
-    return (a != a) ? a : ((b != b) ? b : (a > b ? a : b));
-}
-
 // Maximum of two values that are >= 0 (or NaN with a clear sign bit) on
 // their encodings: for such values the IEEE-754 order is the integer order
-// of the bit patterns, and NaN encodings lie above +inf, so a NaN wins as in
-// nanmax.  Runs on the integer pipe (the FP64 pipe is narrow on this GPU).
+// of the bit patterns, and NaN encodings lie above +inf, so a NaN wins (a
+// non-finite norm is never hidden).  Runs on the integer pipe (the FP64 pipe
+// is narrow on this GPU).
 // With one operand >= 0 the result is max(that operand, other) whenever the
 // other is >= 0, and that operand when the other is negative.
 __device__ __forceinline__ double amax(double a, double b) {
