@@ -9,8 +9,10 @@
  * linear-system step solved on the reduced KKT system eq. (kkt_red_sc),
  * (P + sigma I + rho A'A) x~ = sigma x - q + A'(rho z - y), by warm-started
  * Jacobi-preconditioned conjugate gradient (Algorithm 3, Section 5.3), after
- * Ruiz equilibration (Algorithm 2, Section 5.4), with R = rho I, termination
- * checked every 5 iterations and rho adapted every 10 (Table 1).
+ * Ruiz equilibration (Algorithm 2, Section 5.4), with R = rho I (or OSQP's
+ * per-row rho vector, eq. (rho_vec), with the rho_vector setting),
+ * termination checked every 5 iterations and rho adapted every 10 (Table 1),
+ * and infeasibility detected at every check (Section 3.1).
  *
  * Conventions shared by every call:
  *   - Matrices are CSR with 64-bit row pointers and 32-bit column indices,
@@ -195,8 +197,9 @@ int gbosqp_default_settings(gbosqp_settings *s);
 int osqp_setup(gbosqp_handle **out, const gbosqp_csr *P, const gbosqp_csr *A, const double *q,
                const double *l, const double *u, const gbosqp_settings *settings);
 
-/* Run ADMM from a cold start (x = z = y = 0, rho = rho0) or from the point
- * given by osqp_warm_start, until eq. (termination) holds, an infeasibility
+/* Run ADMM from a cold start (x = z = y = 0, rho = rho0), from the point
+ * given by osqp_warm_start, or (setting warm_start = 1) from the iterates
+ * and rho of the previous solve, until eq. (termination) holds, an infeasibility
  * certificate is found (Section 3.1: at every termination check the
  * differences dx = x^k - x^(k-1), dy = y^k - y^(k-1), scaled to unit
  * inf-norm, are tested against eqs. (prim_infeas) and (dual_infeas) with
