@@ -32,8 +32,20 @@ sys.path.insert(0, ROOT)
 
 METRIC = "time-to-1e-3 solve & ADMM it/s (learned FP32 vs plain FP64); SpMV GB/s"
 WORKLOAD = "lasso_1000x100000"
-WORKLOAD_TEXT = ("Lasso QP: D 100000x1000 at 15% density N(0,1), "
-                 "variables (x, y, t), n = m = 102000, eps_abs = eps_rel = 1e-3")
+WORKLOAD_TEXTS = {
+    "lasso_1000x100000": ("Lasso QP: D 100000x1000 at 15% density N(0,1), variables (x, y, t), "
+                          "n = m = 102000, eps_abs = eps_rel = 1e-3"),
+    "portfolio_100000x1000": ("factor-model portfolio QP: F 100000x1000 at 50% density N(0,1), variables (x, y), "
+                              "n = 101000, m = 101001, eps_abs = eps_rel = 1e-3"),
+    "random_20000x200000": ("random QP: P = M M' + 1e-2 I with M 20000x20000 at 0.05% density, A 200000x20000 at 1% "
+                            "density N(0,1), eps_abs = eps_rel = 1e-3"),
+    "random_100x1000": ("random QP: P = M M' + 1e-2 I with M 100x100 at 15% density, A 1000x100 at 15% density "
+                        "N(0,1), eps_abs = eps_rel = 1e-3"),
+}
+
+
+def workload_text(name: str) -> str:
+    return WORKLOAD_TEXTS.get(name, name)
 HBM_FALLBACK_GBS = 6800.0
 POLICY_PATH = os.path.join(ROOT, "paper_1912_04263_gb300", "policy", "rho_policy.bin")
 
@@ -330,7 +342,7 @@ def gpu_arm(args) -> None:
         "vs_baseline": None,
         "dtype": "f32 (f64 reductions)",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_TEXT, "name": args.workload, "seed": args.seed, "n": n, "m": m,
+        "config": {"workload": workload_text(args.workload), "name": args.workload, "seed": args.seed, "n": n, "m": m,
                    "nnz_A": int(A.nnz), "nnz_P": int(P.nnz), "precision": "fp32", "rho_policy": "learned" if policy is not None else "ratio",
                    "step": "osqp_setup(device CSR) + osqp_solve + solution to device",
                    "l2": "no flush: each step streams >240 MB of matrices, above the 129 MB L2",
@@ -382,7 +394,7 @@ def reference_arm(args) -> None:
         "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": 1, "warmup": 0,
         "ms_per_step": c["seconds"] * 1000.0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_TEXT, "name": args.workload, "seed": args.seed,
+        "config": {"workload": workload_text(args.workload), "name": args.workload, "seed": args.seed,
                    "step": "one full FP64 oracle solve (direct LDL' ADMM); one timed step regardless of --steps "
                            "because one solve takes about a minute on one core"},
         "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
