@@ -49,7 +49,10 @@ extern "C" {
 #define GBOSQP_ERR_NONFINITE (-5)     /* NaN or inf in P, A or q              */
 #define GBOSQP_ERR_CUDA (-6)          /* a CUDA runtime call failed           */
 #define GBOSQP_ERR_OOM (-7)           /* device allocation failed             */
-#define GBOSQP_ERR_DEVICE_TIMEOUT (-8)/* a bounded device wait gave up        */
+#define GBOSQP_ERR_DEVICE_TIMEOUT (-8)/* a bounded device wait gave up (reserved:
+                                         the kernels have no spin-waits; CTAs
+                                         combine results by last-arriver
+                                         tickets, never by waiting)           */
 #define GBOSQP_ERR_UNSUPPORTED (-9)   /* e.g. nnz >= 2^31, no sm_103a device  */
 #define GBOSQP_ERR_POLICY (-10)       /* learned policy parameters invalid    */
 

@@ -155,7 +155,7 @@ struct CsrDev {
     double *lr_part = nullptr;   // 2 partial sums per item
     const int *part = nullptr;   // grid + 1 item boundaries (see partition_items)
     const int2 *lr_cta = nullptr;  // first and last CTA of each long row
-    int *err = nullptr;          // set to 1 if a bulk copy wait timed out
+    int *err = nullptr;          // device error flag (no kernel waits today; kept for bounded waits)
 };
 
 // ------------------------------------------------------------ status block
