@@ -3,8 +3,8 @@
 This package is a plain, slow, direct restatement of the paper's method
 (Schubiger, Banjac, Lygeros, "GPU Acceleration of ADMM for Large-Scale
 Quadratic Programming"), used to check the GPU solver.  Only the tests, the
-package-level ``smoke()`` check and the CPU-baseline leg of ``bench.py`` may
-import it.  It shares no code with the GPU path: no kernels, headers,
+package-level ``smoke()`` check and the CPU-baseline and reference legs of
+``bench.py`` may import it.  It shares no code with the GPU path: no kernels, headers,
 helpers, constants or pre/post-processing.  The GPU path must never import,
 load or call anything here.
 
@@ -13,7 +13,9 @@ Modules:
   admm.py         Ruiz equilibration (Algorithm 2), ADMM (Algorithm 1) with
                   the direct KKT solve, PCG (Algorithm 3) on the reduced KKT
                   system (Section 5.3), residuals and tolerances (Section 3.1),
-                  the Jacobi preconditioner, rho adaptation
+                  infeasibility certificates (Section 3.1), the Jacobi
+                  preconditioner (scalar R or the rho vector of eq. (rho_vec)),
+                  rho adaptation
   checks.py       solution checks that do not run ADMM: the optimality
                   conditions (Section 2.1), brute-force active sets, the
                   closed-form box QP, the duality gap
