@@ -46,6 +46,8 @@ WORKLOAD_TEXTS = {
 
 def workload_text(name: str) -> str:
     return WORKLOAD_TEXTS.get(name, name)
+
+
 HBM_FALLBACK_GBS = 6800.0
 POLICY_PATH = os.path.join(ROOT, "paper_1912_04263_gb300", "policy", "rho_policy.bin")
 
