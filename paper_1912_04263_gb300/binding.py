@@ -63,6 +63,7 @@ class Info(ctypes.Structure):
 
 _lib = None
 _P = ctypes.c_void_p
+_PRECISION: dict = {}  # working precision of each live handle made through this module
 
 
 def lib():
@@ -180,23 +181,52 @@ def osqp_setup(P, A, q, l, u, settings: Settings | None = None, P_is_upper: bool
                           ctypes.byref(s))
     if rc != OK:
         raise GbosqpError(rc, lib().gbosqp_setup_error().decode())
+    _PRECISION[h.value] = int(s.precision)
     return h.value
+
+
+def _device_ptr(t, name: str, dtype: str, numel: int, device: int | None = None) -> int:
+    """Data pointer of a torch tensor that the library reads or writes as
+    numel contiguous elements of dtype in CUDA device memory.  The library
+    cannot see the extent of a device buffer, so a tensor of another element
+    type, on the host, strided, of another length or on another device than
+    the handle's is refused here rather than misread by the kernels."""
+    got = str(t.dtype).replace("torch.", "")
+    if got != dtype:
+        raise TypeError(f"{name}: expected a {dtype} tensor, got {got}")
+    if t.numel() != numel:
+        raise ValueError(f"{name}: expected {numel} elements, got {t.numel()}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: the tensor must be contiguous")
+    if not t.is_cuda:
+        raise ValueError(f"{name}: expected a CUDA tensor, got one on {t.device}")
+    if device is not None and t.device.index != device:
+        raise ValueError(f"{name}: on cuda:{t.device.index}, the solver runs on cuda:{device}")
+    return t.data_ptr()
 
 
 def osqp_setup_device(P_rowptr, P_col, P_val, A_rowptr, A_col, A_val, q, l, u, n: int, m: int,
                       settings: Settings | None = None, P_is_upper: bool = False):
-    """Set up from device-resident arrays (torch CUDA tensors: int64 row
-    pointers, int32 columns, float64 values and vectors)."""
+    """Set up from device-resident arrays (contiguous torch tensors on the
+    settings' CUDA device: int64 row pointers of n + 1 and m + 1 entries,
+    int32 column indices and float64 values of nnz entries each, float64 q
+    of n and l, u of m entries; infinite bounds as +-1e20)."""
     s = settings if settings is not None else default_settings()
     s.P_is_upper = 1 if P_is_upper else 0
     s.input_location = DEVICE
-    cp = Csr(n, n, int(P_val.numel()), P_rowptr.data_ptr(), P_col.data_ptr(), P_val.data_ptr())
-    ca = Csr(m, n, int(A_val.numel()), A_rowptr.data_ptr(), A_col.data_ptr(), A_val.data_ptr())
+    d = s.device
+    nnz_p, nnz_a = int(P_val.numel()), int(A_val.numel())
+    cp = Csr(n, n, nnz_p, _device_ptr(P_rowptr, "P_rowptr", "int64", n + 1, d),
+             _device_ptr(P_col, "P_col", "int32", nnz_p, d), _device_ptr(P_val, "P_val", "float64", nnz_p, d))
+    ca = Csr(m, n, nnz_a, _device_ptr(A_rowptr, "A_rowptr", "int64", m + 1, d),
+             _device_ptr(A_col, "A_col", "int32", nnz_a, d), _device_ptr(A_val, "A_val", "float64", nnz_a, d))
+    qp_, lp, up = (_device_ptr(q, "q", "float64", n, d), _device_ptr(l, "l", "float64", m, d),
+                   _device_ptr(u, "u", "float64", m, d))
     h = ctypes.c_void_p()
-    rc = lib().osqp_setup(ctypes.byref(h), ctypes.byref(cp), ctypes.byref(ca), q.data_ptr(), l.data_ptr(),
-                          u.data_ptr(), ctypes.byref(s))
+    rc = lib().osqp_setup(ctypes.byref(h), ctypes.byref(cp), ctypes.byref(ca), qp_, lp, up, ctypes.byref(s))
     if rc != OK:
         raise GbosqpError(rc, lib().gbosqp_setup_error().decode())
+    _PRECISION[h.value] = int(s.precision)
     return h.value
 
 
@@ -257,8 +287,11 @@ def osqp_get_solution(h):
 
 
 def gbosqp_get_solution_device(h, x, y, z) -> None:
-    """Copy the solution into device tensors (float64, CUDA)."""
-    _check(h, lib().gbosqp_get_solution_device(h, x.data_ptr(), y.data_ptr(), z.data_ptr()))
+    """Copy the solution into device tensors (contiguous float64 CUDA
+    tensors of n, m and m entries)."""
+    n, m = dims(h)[:2]
+    _check(h, lib().gbosqp_get_solution_device(h, _device_ptr(x, "x", "float64", n), _device_ptr(y, "y", "float64", m),
+                                               _device_ptr(z, "z", "float64", m)))
 
 
 def osqp_get_info(h) -> dict:
@@ -269,6 +302,7 @@ def osqp_get_info(h) -> dict:
 
 def osqp_cleanup(h) -> None:
     if h:
+        _PRECISION.pop(h, None)
         lib().osqp_cleanup(h)
 
 
@@ -340,9 +374,20 @@ def gbosqp_bench_kernel(h, kernel: int, reps: int) -> float:
 
 
 def gbosqp_spmv_noalloc(h, which: int, x, y) -> None:
-    """y = M x on device tensors of the handle's working precision, without
-    any device allocation in the call (asynchronous on the handle's stream)."""
-    _check(h, lib().gbosqp_spmv_noalloc(h, int(which), x.data_ptr(), y.data_ptr()))
+    """y = M x on device tensors of the handle's working precision (float32
+    for FP32, float64 for FP64; x of n entries and y of m for MAT_A, x of
+    n + m and y of n for MAT_PAT), without any device allocation in the call
+    (asynchronous on the handle's stream)."""
+    n, m = dims(h)[:2]
+    nin, nout = (n, m) if which == MAT_A else (n + m, n)
+    prec = _PRECISION.get(h)
+    if prec is None:  # a handle made by a direct library call: take the tensor's type
+        dt = str(x.dtype).replace("torch.", "")
+        if dt not in ("float32", "float64"):
+            raise TypeError(f"x: expected a float32 or float64 tensor, got {dt}")
+    else:
+        dt = "float32" if prec == FP32 else "float64"
+    _check(h, lib().gbosqp_spmv_noalloc(h, int(which), _device_ptr(x, "x", dt, nin), _device_ptr(y, "y", dt, nout)))
 
 
 def _f32(a, shape=None):
