@@ -96,25 +96,31 @@ class ClockSampler:
         self.device = device
         self.proc = None
         self.path = None
+        self.out = None
 
     def start(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
+        self.out = open(self.path, "w")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
                                           "--format=csv,noheader,nounits", "-lms", "100"],
-                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
     def stop(self) -> dict:
         if self.proc is None:
+            self.out.close()
+            os.unlink(self.path)
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
+            self.proc.wait()
+        self.out.close()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.path) as f:
@@ -327,10 +333,11 @@ def gpu_arm(args) -> None:
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.txt")
     if os.path.exists(tpath):
-        for line in open(tpath):
-            parts = line.split()
-            if len(parts) >= 3 and parts[0] == dominant and parts[1] == args.workload:
-                traffic = float(parts[2])
+        with open(tpath) as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) >= 3 and parts[0] == dominant and parts[1] == args.workload:
+                    traffic = float(parts[2])
     out = {
         "metric": METRIC,
         "value": replicas.job_throughput(args.steps, world, ms_step * args.steps / 1000.0),

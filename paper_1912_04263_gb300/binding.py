@@ -459,7 +459,8 @@ def save_policy(path: str, params) -> None:
 
 def load_policy(path: str) -> np.ndarray:
     import zlib
-    raw = open(path, "rb").read()
+    with open(path, "rb") as fh:
+        raw = fh.read()
     if raw[:8] != POLICY_MAGIC:
         raise ValueError(f"{path}: not a policy file")
     count = int(np.frombuffer(raw[8:12], "<u4")[0])

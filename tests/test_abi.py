@@ -21,7 +21,8 @@ def lib():
 
 
 def declared_functions():
-    text = open(os.path.join(ROOT, "include", "gbosqp.h")).read()
+    with open(os.path.join(ROOT, "include", "gbosqp.h")) as f:
+        text = f.read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     names = re.findall(r"^\s*(?:const\s+)?(?:int|void|char)\s*\*?\s*(\w+)\s*\(", text, flags=re.M)
     return sorted(set(names))
@@ -56,7 +57,8 @@ def test_settings_struct_layout_matches_the_header(lib):
     """The ctypes mirror of gbosqp_settings has the header's field order (so
     the binding and the C struct agree byte for byte)."""
     from paper_1912_04263_gb300 import binding as gb
-    text = open(os.path.join(ROOT, "include", "gbosqp.h")).read()
+    with open(os.path.join(ROOT, "include", "gbosqp.h")) as f:
+        text = f.read()
     body = text[text.index("typedef struct {\n    double alpha;"):]
     body = body[:body.index("} gbosqp_settings;")]
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)

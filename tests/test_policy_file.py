@@ -23,14 +23,14 @@ def test_corrupt_or_foreign_files_are_refused(tmp_path):
     p = np.ones(gb.POLICY_PARAMS, np.float32)
     path = str(tmp_path / "w.bin")
     gb.save_policy(path, p)
-    raw = bytearray(open(path, "rb").read())
+    raw = bytearray((tmp_path / "w.bin").read_bytes())
     raw[100] ^= 0x40  # flip a payload bit: the CRC no longer matches
     bad = str(tmp_path / "bad.bin")
-    open(bad, "wb").write(bytes(raw))
+    (tmp_path / "bad.bin").write_bytes(bytes(raw))
     with pytest.raises(ValueError):
         gb.load_policy(bad)
     other = str(tmp_path / "other.bin")
-    open(other, "wb").write(b"NOTAPOLICYFILE" + bytes(16))
+    (tmp_path / "other.bin").write_bytes(b"NOTAPOLICYFILE" + bytes(16))
     with pytest.raises(ValueError):
         gb.load_policy(other)
 
