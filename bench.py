@@ -97,34 +97,19 @@ class ClockSampler:
         self.proc = None
         self.path = None
         self.out = None
-        self.skip = 0
 
-    def _rows(self) -> list:
-        with open(self.path) as f:
-            return [line for line in f if line.endswith("\n")]
-
-    def start(self, ready_timeout: float = 3.0):
-        """Start sampling and return once the first row is out (at most
-        ready_timeout seconds), so that the rows that follow fall inside the
-        timed region that starts next; stop() keeps only those."""
+    def start(self):
+        """Start sampling right before the timed region: every row nvidia-smi
+        prints before stop() falls inside it."""
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         self.out = open(self.path, "w")
-        self.skip = 0
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
                                           "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.out, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
-            return
-        t0 = time.time()
-        while time.time() - t0 < ready_timeout and self.proc.poll() is None:
-            n = len(self._rows())
-            if n:
-                self.skip = n
-                break
-            time.sleep(0.01)
 
     def stop(self) -> dict:
         if self.proc is None:
@@ -138,29 +123,24 @@ class ClockSampler:
             self.proc.kill()
             self.proc.wait()
         self.out.close()
-        rows = self._rows()
-        window = "timed region"
-        if len(rows) > self.skip:
-            rows = rows[self.skip:]
-        else:  # no row came out during the timed region: report the nearest ones
-            window = "just before the timed region"
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in rows:
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
         os.unlink(self.path)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm), "window": window}
+                "reasons": sorted(reasons), "samples": len(sm)}
 
 
 # ------------------------------------------------------------- GPU arm --
