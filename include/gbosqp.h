@@ -192,7 +192,10 @@ int gbosqp_default_settings(gbosqp_settings *s);
  * explicitly, Section 5.2) and the concatenated [P A'] in CSR, run Ruiz
  * equilibration (Algorithm 2) on the device, compute the Jacobi
  * preconditioner data (Section 5.3.1), and build the solve graph.
- * P: n x n (upper triangle or full, see P_is_upper), A: m x n, q: n, l, u: m.
+ * P: n x n (upper triangle or full, see P_is_upper), A: m x n, q: n, l, u: m,
+ * with n >= 1 and m >= 0: m = 0 is a problem without constraints (A has no
+ * rows; l and u must still be non-NULL but no element is read), and P may
+ * have no nonzeros (a linear program).
  * Memory location of all inputs: settings->input_location.  On success *out
  * owns all device memory until osqp_cleanup.  On failure *out is NULL and
  * the code says why (no handle exists to query gbosqp_last_error; the text
