@@ -407,7 +407,7 @@ def reference_arm(args) -> None:
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_text(args.workload), "name": args.workload, "seed": args.seed,
                    "step": "one full FP64 oracle solve (direct LDL' ADMM); one timed step regardless of --steps "
-                           "because one solve takes about a minute on one core"},
+                           "because one solve of the Lasso workload takes about half a minute on one core"},
         "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
                          "sample": "one full solve of the same instance, single thread"},
         "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
