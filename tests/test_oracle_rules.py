@@ -162,3 +162,34 @@ def test_objective_error_bound_holds_at_random_points(seed):
             dual_needed |= err > prim_only * (1 + 1e-6) + 1e-12
     assert dual_needed
     assert checks.objective_error_bound(xs, ys, 0.0, 0.0, xs, ys) == 0.0
+
+
+# ------------------------------------------------ MLP forward (policy) --
+
+def _hand_network():
+    """Layer 1 copies the 4 inputs into units 0-3; layer 2 rotates them
+    (unit i takes unit (i + 1) mod 4); layer 3 weighs them.  With input
+    x, h1 = relu(x) and h2_i = relu(x_{(i+1) mod 4}) on units 0-3, so
+    o0 = 1 h2_0 - 1 h2_1 + 2 h2_2 + 0.5 h2_3 + 0.25 and
+    o1 = h2_3 - 1."""
+    p = {k: np.zeros(s) for k, s in mlp.PARAM_SHAPES.items()}
+    for i in range(4):
+        p["W1"][i, i] = 1.0
+        p["W2"][i, (i + 1) % 4] = 1.0
+    p["W3"][0, :4] = [1.0, -1.0, 2.0, 0.5]
+    p["W3"][1, 3] = 1.0
+    p["b3"][:] = [0.25, -1.0]
+    return p
+
+
+@pytest.mark.parametrize("x,o", [
+    ([1.0, 2.0, -3.0, 4.0], [2.0 - 0.0 + 2.0 * 4.0 + 0.5 * 1.0 + 0.25, 1.0 - 1.0]),   # h2 = (2, 0, 4, 1)
+    ([-1.0, -2.0, 0.5, 0.25], [0.0 - 0.5 + 0.5 + 0.0 + 0.25, 0.0 - 1.0]),             # h2 = (0, .5, .25, 0)
+    ([3.0, 0.0, 0.0, -8.0], [0.0 - 0.0 + 0.0 + 0.5 * 3.0 + 0.25, 3.0 - 1.0]),          # h2 = (0, 0, 0, 3)
+])
+def test_mlp_forward_on_a_hand_built_network(x, o):
+    p = _hand_network()
+    out, _ = mlp.forward(p, np.array([x]))
+    assert out[0].tolist() == o
+    # every value here is exact in BF16, so the BF16 forward gives the same numbers
+    assert mlp.forward_bf16(p, np.array([x]))[0].tolist() == o
