@@ -193,3 +193,14 @@ def test_mlp_forward_on_a_hand_built_network(x, o):
     assert out[0].tolist() == o
     # every value here is exact in BF16, so the BF16 forward gives the same numbers
     assert mlp.forward_bf16(p, np.array([x]))[0].tolist() == o
+
+
+def test_masked_mse_loss_by_hand():
+    """loss = sum_k w_k (o_k - t_k)^2 / (2B) with B = 2 samples:
+    (1 * 1^2 + 0.5 * 2^2 + 0 * 3^2 + 2 * (-1)^2) / 4 = 5 / 4; dL/do = w (o - t) / B."""
+    out = np.array([[1.0, 2.0], [3.0, -1.0]])
+    tgt = np.zeros((2, 2))
+    w = np.array([[1.0, 0.5], [0.0, 2.0]])
+    loss, g = mlp.loss_and_grad_out(out, tgt, w)
+    assert loss == 1.25
+    assert g.tolist() == [[0.5, 0.5], [0.0, -1.0]]
