@@ -22,5 +22,9 @@ Modules:
   formats.py      COO / CSR / CSC conversions of Section 4.3
   mlp.py          FP64 forward / backward / Adam for the rho-policy MLP
                   (parity unpinned against the paper: the paper has no MLP;
-                  pinned by finite differences)
+                  pinned by finite differences and a hand-built network)
+  policy.py       the learned rho decision and its stall rule, restated from
+                  the solver's readings (parity unpinned against the paper;
+                  pinned by hand-built networks and a hand-traced stall
+                  sequence)
 """
