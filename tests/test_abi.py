@@ -106,3 +106,32 @@ def test_objective_error_bound_holds_on_loose_iterates():
         bound = checks.objective_error_bound(r.x, r.y, v.prim, v.dual, xs, ys)
         assert abs(r.obj - fs) <= bound * (1 + 1e-9) + 1e-12
     assert checked >= 3
+
+
+def test_binding_constants_match_the_header():
+    """Every #define of include/gbosqp.h that the binding mirrors has the same
+    value there (error codes, statuses, enumerations, sizes, kernel
+    selectors)."""
+    from paper_1912_04263_gb300 import binding as gb
+    with open(os.path.join(ROOT, "include", "gbosqp.h")) as f:
+        text = f.read()
+    defs = {}
+    for name, val in re.findall(r"^#define\s+GBOSQP_(\w+)\s+\(?(-?[0-9.e]+)\)?", text, flags=re.M):
+        defs[name] = float(val) if ("." in val or "e" in val) else int(val)
+    pairs = {"OK": gb.OK, "ERR_INVALID_ARG": gb.ERR_INVALID_ARG, "ERR_DIMENSION": gb.ERR_DIMENSION,
+             "ERR_CSR": gb.ERR_CSR, "ERR_BOUNDS": gb.ERR_BOUNDS, "ERR_NONFINITE": gb.ERR_NONFINITE,
+             "ERR_CUDA": gb.ERR_CUDA, "ERR_OOM": gb.ERR_OOM, "ERR_DEVICE_TIMEOUT": gb.ERR_DEVICE_TIMEOUT,
+             "ERR_UNSUPPORTED": gb.ERR_UNSUPPORTED, "ERR_POLICY": gb.ERR_POLICY,
+             "SOLVED": gb.SOLVED, "MAX_ITER": gb.MAX_ITER, "NONFINITE": gb.NONFINITE,
+             "PRIMAL_INFEASIBLE": gb.PRIMAL_INFEASIBLE, "DUAL_INFEASIBLE": gb.DUAL_INFEASIBLE,
+             "FP32": gb.FP32, "FP64": gb.FP64, "RHO_RATIO": gb.RHO_RATIO, "RHO_LEARNED": gb.RHO_LEARNED,
+             "RHO_FIXED": gb.RHO_FIXED, "HOST": gb.HOST, "DEVICE": gb.DEVICE, "LOOP_GRAPH": gb.LOOP_GRAPH,
+             "LOOP_HOST": gb.LOOP_HOST, "MAT_A": gb.MAT_A, "MAT_PAT": gb.MAT_PAT,
+             "CHECK_FIELDS": gb.CHECK_FIELDS, "POLICY_PARAMS": gb.POLICY_PARAMS, "INFINITY": gb.INFINITY,
+             "K_PCG_DIRECTION": gb.K_PCG_DIRECTION, "K_PCG_KAPPLY": gb.K_PCG_KAPPLY, "K_PCG_UPDATE": gb.K_PCG_UPDATE,
+             "K_PCG_INIT": gb.K_PCG_INIT, "K_ADMM_UPDATE": gb.K_ADMM_UPDATE, "K_CHECK_A": gb.K_CHECK_A,
+             "K_CHECK_B": gb.K_CHECK_B, "K_INF_A": gb.K_INF_A, "K_INF_B": gb.K_INF_B}
+    for name, value in pairs.items():
+        assert name in defs, name
+        assert defs[name] == value, (name, defs[name], value)
+    assert len(gb.CHECK_NAMES) <= gb.CHECK_FIELDS
