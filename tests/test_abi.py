@@ -135,3 +135,28 @@ def test_binding_constants_match_the_header():
         assert name in defs, name
         assert defs[name] == value, (name, defs[name], value)
     assert len(gb.CHECK_NAMES) <= gb.CHECK_FIELDS
+
+
+@pytest.mark.parametrize("struct,cls", [("gbosqp_info", "Info"), ("gbosqp_csr", "Csr")])
+def test_info_and_csr_struct_layouts_match_the_header(struct, cls):
+    """Field names in declaration order (several per line allowed) equal the
+    ctypes mirror's, and the mirror's types have the header's widths."""
+    from paper_1912_04263_gb300 import binding as gb
+    with open(os.path.join(ROOT, "include", "gbosqp.h")) as f:
+        text = f.read()
+    body = text[:text.index("} " + struct + ";")]
+    body = body[body.rindex("typedef struct {"):]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = []
+    widths = {"int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "double": ctypes.c_double}
+    decl = re.findall(r"(?:const\s+)?(int32_t|int64_t|double)\s*([\w\s,*]+);", body)
+    expect_types = []
+    for typ, names in decl:
+        for nm in names.split(","):
+            nm = nm.strip()
+            fields.append(nm.lstrip("*").strip())
+            expect_types.append(ctypes.c_void_p if nm.startswith("*") else widths[typ])
+    mirror = getattr(gb, cls)._fields_
+    assert [f for f, _ in mirror] == fields
+    for (f, t), e in zip(mirror, expect_types):
+        assert ctypes.sizeof(t) == ctypes.sizeof(e), f
