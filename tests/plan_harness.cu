@@ -1,8 +1,12 @@
 // Host-only check of the SpMV work plan (build_plan) and of the CTA
 // partition (partition_items) on seeded random row-length profiles; prints
 // "ok" or the first violated invariant.  Built and run by
-// tests/test_host_plan.py (no GPU needed).
+// tests/test_host_plan.py (no GPU needed).  With --time it instead times
+// both on the row-length profiles of the 100000 x 1000 Lasso workload's A and
+// [P A'] (the per-set-up host cost of the plans).
+#include <chrono>
 #include <cstdio>
+#include <cstring>
 #include <random>
 #include <vector>
 
@@ -14,7 +18,39 @@ static int group_width_of(long long avg) {
     return avg >= 24 ? 32 : avg >= 12 ? 16 : avg >= 6 ? 8 : avg >= 3 ? 4 : 1;
 }
 
-int main() {
+template <class F>
+static double mean_ms(F f, int reps) {
+    const auto t0 = std::chrono::steady_clock::now();
+    for (int k = 0; k < reps; ++k) f();
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count() / reps;
+}
+
+// Row lengths of the Lasso workload: A has 100000 rows of 1 + Binomial(1000,
+// 0.15) nonzeros and 2000 rows of 2; [P A'] has 1000 rows of 2 +
+// Binomial(100000, 0.15), then 101000 rows of 2.
+static int time_lasso_plans() {
+    std::mt19937 rng(1);
+    std::binomial_distribution<int> row(1000, 0.15), col(100000, 0.15);
+    std::vector<int> rpA(1, 0), rpP(1, 0);
+    for (int r = 0; r < 100000; ++r) rpA.push_back(rpA.back() + row(rng) + 1);
+    for (int r = 0; r < 2000; ++r) rpA.push_back(rpA.back() + 2);
+    for (int r = 0; r < 1000; ++r) rpP.push_back(rpP.back() + col(rng) + 2);
+    for (int r = 0; r < 101000; ++r) rpP.push_back(rpP.back() + 2);
+    const char *names[2] = {"A", "[P A']"};
+    const std::vector<int> *rps[2] = {&rpA, &rpP};
+    for (int i = 0; i < 2; ++i) {
+        HostPlan hp = build_plan(*rps[i]);
+        const double b = mean_ms([&] { hp = build_plan(*rps[i]); }, 200);
+        const double p608 = mean_ms([&] { volatile size_t n = partition_items(hp, 608).part.size(); (void)n; }, 200);
+        const double p456 = mean_ms([&] { volatile size_t n = partition_items(hp, 456).part.size(); (void)n; }, 200);
+        printf("%s: %zu items, %zu long rows; build_plan %.3f ms, partition(608) %.3f ms, partition(456) %.3f ms\n",
+               names[i], hp.items.size(), hp.longrows.size(), b, p608, p456);
+    }
+    return 0;
+}
+
+int main(int argc, char **argv) {
+    if (argc > 1 && std::strcmp(argv[1], "--time") == 0) return time_lasso_plans();
     std::mt19937 rng(12345);
     for (int trial = 0; trial < 400; ++trial) {
         const int nrows = 1 + (int)(rng() % 4000);
