@@ -241,8 +241,10 @@ def main():
     report = {"train_trajectories": int(done),
               "train_families": "random n in [500, 2500] (half), Lasso f in [50, 400] x 20f, portfolio "
                                 "[2000, 10000] assets x [20, 100] factors",
-              "samples": int(len(S)), "loss_first": float(hist[:50].mean()), "loss_last": float(hist[-50:].mean()),
+              "samples": int(len(S)), "train_steps": int(args.steps), "batch": 256,
+              "loss_first": float(hist[:50].mean()), "loss_last": float(hist[-50:].mean()),
               "label_mult_hist": np.histogram(S[:, 4], bins=[-3, -1.7, -0.5, 0.5, 1.7, 3])[0].tolist(),
+              "label_mult_hist_bins": "rho multiplier x1/10, x1/3, x1, x3, x10",
               "summary": summary, "rows": rows, "seconds": time.time() - t0}
     with open(os.path.join(args.out, "eval.json"), "w") as fh:
         json.dump(report, fh, indent=1)
