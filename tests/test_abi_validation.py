@@ -62,6 +62,19 @@ def test_malformed_problems_are_refused_on_the_host(lib, parts, which, change, c
     assert words in msg and not h
 
 
+def test_too_many_variables_and_constraints_are_refused(lib):
+    """[P A'] has n + m columns and the joint vectors n + m entries, all
+    indexed with 32-bit integers: n + m must stay below 2^31 - 64.  The
+    arrays are not read before the sizes are checked."""
+    n, m = 1_200_000_000, 1_000_000_000
+    rp = np.zeros(2, np.int64)
+    v = np.zeros(1)
+    P = gb.Csr(n, n, 0, rp.ctypes.data, None, None)
+    A = gb.Csr(m, n, 0, rp.ctypes.data, None, None)
+    rc, h, msg = _setup(lib, P, A, v, v, v)
+    assert rc == gb.ERR_UNSUPPORTED and "n + m" in msg and not h
+
+
 def test_null_vectors_are_refused(lib, parts):
     qp, hp, ha = parts
     q, l, u = (np.ascontiguousarray(v, dtype=np.float64) for v in (qp.q, qp.l, qp.u))
