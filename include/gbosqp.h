@@ -194,7 +194,8 @@ int gbosqp_default_settings(gbosqp_settings *s);
  * preconditioner data (Section 5.3.1), and build the solve graph.
  * P: n x n (upper triangle or full, see P_is_upper), A: m x n, q: n, l, u: m,
  * with n >= 1, m >= 0 and n + m < 2^31 - 64 (GBOSQP_ERR_UNSUPPORTED otherwise,
- * as for nnz >= 2^31 in one matrix): m = 0 is a problem without constraints (A has no
+ * as for nnz >= 2^31 in one matrix, or nnz >= 2^30 in an upper-triangular P,
+ * whose full form is built with 32-bit offsets): m = 0 is a problem without constraints (A has no
  * rows; l and u must still be non-NULL but no element is read), and P may
  * have no nonzeros (a linear program).
  * Memory location of all inputs: settings->input_location.  On success *out

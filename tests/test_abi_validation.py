@@ -75,6 +75,22 @@ def test_too_many_variables_and_constraints_are_refused(lib):
     assert rc == gb.ERR_UNSUPPORTED and "n + m" in msg and not h
 
 
+def test_an_upper_triangle_whose_full_form_could_overflow_is_refused(lib):
+    """The full P built from an upper triangle has up to twice its
+    nonzeros, with 32-bit offsets: an upper triangle of 2^30 or more
+    nonzeros is refused before any array is read (a full P of the same size
+    is accepted by this check)."""
+    rp = np.zeros(2, np.int64)
+    v = np.zeros(1)
+    ci = np.zeros(1, np.int32)
+    P = gb.Csr(1000, 1000, 1 << 30, rp.ctypes.data, ci.ctypes.data, v.ctypes.data)
+    A = gb.Csr(0, 1000, 0, rp.ctypes.data, None, None)
+    s = gb.default_settings()
+    s.P_is_upper = 1
+    rc, h, msg = _setup(lib, P, A, v, v, v, s)
+    assert rc == gb.ERR_UNSUPPORTED and "upper-triangular" in msg and not h
+
+
 def test_null_vectors_are_refused(lib, parts):
     qp, hp, ha = parts
     q, l, u = (np.ascontiguousarray(v, dtype=np.float64) for v in (qp.q, qp.l, qp.u))
