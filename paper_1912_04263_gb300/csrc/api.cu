@@ -121,11 +121,12 @@ int osqp_setup(gbosqp_handle **out, const gbosqp_csr *P, const gbosqp_csr *A, co
     if (n <= 0 || P->ncols != n) return bad(GBOSQP_ERR_DIMENSION, "P must be n x n with n > 0");
     if (m < 0 || A->ncols != n) return bad(GBOSQP_ERR_DIMENSION, "A must be m x n");
     if (P->nnz < 0 || A->nnz < 0) return bad(GBOSQP_ERR_CSR, "negative nnz");
-    if (P->nnz >= (1LL << 31) || A->nnz >= (1LL << 31))
-        return bad(GBOSQP_ERR_UNSUPPORTED, "more than 2^31-1 nonzeros in one matrix");
-    if (s.P_is_upper && 2 * P->nnz >= (1LL << 31))  // the full P has at most twice the upper triangle's entries
+    // 64 below 2^31: item bounds rounded outward to 16 bytes stay within 32-bit offsets
+    if (P->nnz >= (1LL << 31) - 64 || A->nnz >= (1LL << 31) - 64)
+        return bad(GBOSQP_ERR_UNSUPPORTED, "2^31 - 64 or more nonzeros in one matrix");
+    if (s.P_is_upper && 2 * P->nnz >= (1LL << 31) - 64)  // the full P has at most twice the upper triangle's entries
         return bad(GBOSQP_ERR_UNSUPPORTED,
-                   "an upper-triangular P must have fewer than 2^30 nonzeros (its full form uses 32-bit offsets)");
+                   "an upper-triangular P must have fewer than 2^30 - 32 nonzeros (its full form uses 32-bit offsets)");
     if ((int64_t)n + (int64_t)m >= (1LL << 31) - 64)
         return bad(GBOSQP_ERR_UNSUPPORTED, "n + m must be below 2^31 (the columns of [P A'] and the joint vectors)");
     if (!P->rowptr || (P->nnz && (!P->colind || !P->val)) || !A->rowptr || (A->nnz && (!A->colind || !A->val)))

@@ -726,8 +726,8 @@ SetupData device_setup(const gbosqp_csr &P, const gbosqp_csr &A, const double *q
 
     // ---- 4. [P A'], Jacobi data, q norms
     sd.nnzPAt = Pf.nnz + At.nnz;
-    if (sd.nnzPAt >= (1LL << 31) || A.nnz >= (1LL << 31))
-        fail(GBOSQP_ERR_UNSUPPORTED, "more than 2^31-1 nonzeros in A or [P A']");
+    if (sd.nnzPAt >= (1LL << 31) - 64 || A.nnz >= (1LL << 31) - 64)
+        fail(GBOSQP_ERR_UNSUPPORTED, "2^31 - 64 or more nonzeros in A or [P A']");
     sd.PAt_rowptr.alloc((size_t)(n + 1) * sizeof(int));
     sd.PAt_pend.alloc((size_t)std::max(n, 1) * sizeof(int));
     sd.PAt_col.alloc((sd.nnzPAt + 8) * sizeof(int));  // 8 elements of slack: loads rounded outward to 16 bytes stay inside

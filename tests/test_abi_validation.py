@@ -48,6 +48,7 @@ def _csr(base, **kw):
     ("A", dict(nrows=-1), "ERR_DIMENSION", "m x n"),
     ("P", dict(nnz=-3), "ERR_CSR", "negative nnz"),
     ("A", dict(nnz=1 << 31), "ERR_UNSUPPORTED", "2^31"),
+    ("A", dict(nnz=(1 << 31) - 64), "ERR_UNSUPPORTED", "2^31 - 64"),
     ("P", dict(rowptr=None), "ERR_INVALID_ARG", "NULL CSR"),
     ("A", dict(colind=None), "ERR_INVALID_ARG", "NULL CSR"),
     ("A", dict(val=None), "ERR_INVALID_ARG", "NULL CSR"),
@@ -77,9 +78,8 @@ def test_too_many_variables_and_constraints_are_refused(lib):
 
 def test_an_upper_triangle_whose_full_form_could_overflow_is_refused(lib):
     """The full P built from an upper triangle has up to twice its
-    nonzeros, with 32-bit offsets: an upper triangle of 2^30 or more
-    nonzeros is refused before any array is read (a full P of the same size
-    is accepted by this check)."""
+    nonzeros, with 32-bit offsets: an upper triangle of 2^30 - 32 or more
+    nonzeros is refused before any array is read."""
     rp = np.zeros(2, np.int64)
     v = np.zeros(1)
     ci = np.zeros(1, np.int32)
