@@ -121,7 +121,7 @@ int osqp_setup(gbosqp_handle **out, const gbosqp_csr *P, const gbosqp_csr *A, co
     if (n <= 0 || P->ncols != n) return bad(GBOSQP_ERR_DIMENSION, "P must be n x n with n > 0");
     if (m < 0 || A->ncols != n) return bad(GBOSQP_ERR_DIMENSION, "A must be m x n");
     if (P->nnz < 0 || A->nnz < 0) return bad(GBOSQP_ERR_CSR, "negative nnz");
-    // 64 below 2^31: item bounds rounded outward to 16 bytes stay within 32-bit offsets
+    // offsets into the matrix arrays are 32-bit ints; 64 below 2^31 leaves headroom at the arrays' ends
     if (P->nnz >= (1LL << 31) - 64 || A->nnz >= (1LL << 31) - 64)
         return bad(GBOSQP_ERR_UNSUPPORTED, "2^31 - 64 or more nonzeros in one matrix");
     if (s.P_is_upper && 2 * P->nnz >= (1LL << 31) - 64)  // the full P has at most twice the upper triangle's entries
