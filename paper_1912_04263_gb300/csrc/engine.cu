@@ -1371,7 +1371,7 @@ private:
 
     DevBuf convert(DevBuf &&src, long long count) {
         if (sizeof(T) == sizeof(double)) return std::move(src);
-        DevBuf out(sizeof(T) * (count + 8));  // 8 elements of slack past the last nonzero, as the set-up arrays
+        DevBuf out(sizeof(T) * (count + 8));  // 8 elements of slack past the last nonzero, like the set-up arrays
         if (count) launch(k_from_double<T>, ceil_div(count, 256), 256, stream_, src.as<double>(), out.as<T>(), count);
         GB_CUDA(cudaGetLastError());
         return out;  // src is released after the conversion in stream order
