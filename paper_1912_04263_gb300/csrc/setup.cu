@@ -731,7 +731,7 @@ SetupData device_setup(const gbosqp_csr &P, const gbosqp_csr &A, const double *q
         fail(GBOSQP_ERR_UNSUPPORTED, "2^31 - 64 or more nonzeros in A or [P A']");
     sd.PAt_rowptr.alloc((size_t)(n + 1) * sizeof(int));
     sd.PAt_pend.alloc((size_t)std::max(n, 1) * sizeof(int));
-    // 8 elements of slack past the last nonzero, as for A
+    // 8 elements of slack past the last nonzero, as in the input copies
     sd.PAt_col.alloc((sd.nnzPAt + 8) * sizeof(int));
     sd.PAt_val.alloc((sd.nnzPAt + 8) * sizeof(double));
     launch(k_pat_rowptr, blocks_for(n + 1, 256), 256, st, Pf.rp.as<int>(), At.rp.as<int>(), n,
