@@ -949,7 +949,7 @@ public:
         solve_ms_ = ms;
         Status h = read_status();
         last_ = h;
-        if (h.device_error) fail(GBOSQP_ERR_DEVICE_TIMEOUT, "a device wait for a bulk copy timed out");
+        if (h.device_error) fail(GBOSQP_ERR_DEVICE_TIMEOUT, "a bounded device wait gave up");
         solve_launches = g_launches - before;
         if (exec_) {
             // kernels executed by the graph: reset, output, per iteration
