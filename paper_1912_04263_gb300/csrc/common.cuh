@@ -5,7 +5,7 @@
 // * DevBuf: owning device allocation.
 // * Status: the device-resident scalar block of a solve (rho, PCG scalars,
 //   check results, flags), so that the iteration loop needs no host
-//   round trip (north of Algorithm 1: every decision is taken on the device).
+//   round trip: every decision of Algorithm 1 is taken on the device.
 // * Row-block CSR SpMV: the rows of a CSR matrix are cut at set-up into work
 //   items of at most kCap nonzeros (consecutive short rows), and rows longer
 //   than kCap are cut into pieces whose partial sums are combined in a fixed
