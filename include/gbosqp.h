@@ -391,17 +391,19 @@ int gbosqp_bench_kernel(gbosqp_handle *h, int kernel, int32_t reps, double *avg_
  *   x, y   device arrays on the handle's device, of float on an FP32 handle
  *          and double on an FP64 handle; caller-owned; may not overlap
  *
- * Allocates nothing: the scratch that combines the pieces of long rows is a
- * fixed device array inside the library (2.5 MiB, resident on every device
- * that loads the library until the process exits), which holds up to 131072
- * work items and 131072 long rows per matrix; a larger matrix is rejected
- * with GBOSQP_ERR_UNSUPPORTED.  The first call on each device looks up that
- * array's device address; make that first call before any stream capture.
- * Every call shares the array (its counters are cleared at the start of each
- * call and it keeps the last call's partial sums), so calls that overlap on
- * the GPU, from any thread or handle, race: serialise them.  The work is
- * queued on the handle's stream and the call returns without waiting;
- * synchronise that stream (or the device) before reading y. */
+ * Allocates nothing: the scratch that combines the parts of rows cut between
+ * warps is a fixed device array inside the library (1 MiB, resident on every
+ * device that loads the library until the process exits), enough for the
+ * launch of any GPU with up to about 20000 resident warps; a plan that needs
+ * more is rejected with GBOSQP_ERR_UNSUPPORTED.  The first call on each
+ * device looks up that array's device address and keeps it for the process;
+ * make that first call before any stream capture, and do not use this call
+ * across a device reset (cudaDeviceReset) in the same process.  Every call
+ * shares the array (its tickets are cleared at the start of each call and it
+ * keeps the last call's partial sums), so calls that overlap on the GPU, from
+ * any thread or handle, race: serialise them.  The work is queued on the
+ * handle's stream and the call returns without waiting; synchronise that
+ * stream (or the device) before reading y. */
 int gbosqp_spmv_noalloc(gbosqp_handle *h, int which, const void *x, void *y);
 
 #ifdef __cplusplus

@@ -128,7 +128,7 @@ int osqp_setup(gbosqp_handle **out, const gbosqp_csr *P, const gbosqp_csr *A, co
         return bad(GBOSQP_ERR_UNSUPPORTED,
                    "an upper-triangular P must have fewer than 2^30 - 32 nonzeros (its full form uses 32-bit offsets)");
     if ((int64_t)n + (int64_t)m >= (1LL << 31) - 64)
-        return bad(GBOSQP_ERR_UNSUPPORTED, "n + m must be below 2^31 (the columns of [P A'] and the joint vectors)");
+        return bad(GBOSQP_ERR_UNSUPPORTED, "n + m must be below 2^31 - 64 (the columns of [P A'] and the joint vectors)");
     if (!P->rowptr || (P->nnz && (!P->colind || !P->val)) || !A->rowptr || (A->nnz && (!A->colind || !A->val)))
         return bad(GBOSQP_ERR_INVALID_ARG, "NULL CSR array");
     std::unique_ptr<gbosqp_handle> h(new gbosqp_handle());

@@ -6,13 +6,8 @@
 // * Status: the device-resident scalar block of a solve (rho, PCG scalars,
 //   check results, flags), so that the iteration loop needs no host
 //   round trip: every decision of Algorithm 1 is taken on the device.
-// * Row-block CSR SpMV: the rows of a CSR matrix are cut at set-up into work
-//   items of at most kCap nonzeros (consecutive short rows), and rows longer
-//   than kCap are cut into pieces whose partial sums are combined in a fixed
-//   order by the last piece to finish.  A CTA streams an item's contiguous
-//   value/column range with coalesced loads, multiplies by the gathered
-//   vector into shared memory, then reduces each row with a lane group sized
-//   to the item's mean row length.  Results are bitwise reproducible.
+// * The CSR SpMV core itself (warp-stream kernels and their plan) is in
+//   spmv.cuh; this file keeps the reductions it uses.
 // * Block reductions with a last-block finalize: per-CTA partials are summed
 //   in CTA order by the last CTA to finish (FP64 sums, NaN-propagating max).
 #pragma once
@@ -90,73 +85,14 @@ struct PoolScope {
 
 // -------------------------------------------------------------- constants
 
-constexpr int kThreads = 256;             // CTA size of every row-block kernel
+constexpr int kThreads = 256;             // CTA size of every kernel of the solve
 constexpr int kWarps = kThreads / 32;
-#ifndef GB_CAP
-#define GB_CAP 2048
-#endif
-constexpr int kCap = GB_CAP;              // max nonzeros per work item
-// Fixed cost of a work item in nonzero-equivalents (descriptor, barriers,
-// epilogue latency), used to give every CTA an equal share of the work.
-// Measured on GB300 an item costs about the same whatever its nonzero
-// count (items of 512 and of 2048 nonzeros take about equally long), so the
-// fixed part dominates: CTAs get equal item counts, nonzeros break ties.
-#ifndef GB_ITEM_COST
-#define GB_ITEM_COST (1 << 20)
-#endif
-constexpr long long kItemCost = GB_ITEM_COST;
-constexpr int kPerThread = kCap / kThreads;
 constexpr double kInf = 1e20;             // |bound| >= kInf is infinite
-
-// ------------------------------------------------------------ SpMV items
-
-struct Item {
-    int r0;  // first row (block) or the long row (piece)
-    int r1;  // one past the last row (block, >= 0) or -(long-row id + 1)
-    int k0;  // first nonzero
-    int k1;  // one past the last nonzero
-};
-
-struct LongRow {
-    int first_item;
-    int npieces;
-};
-
-// Host-side plan of one matrix: items and the long-row table.
-struct HostPlan {
-    std::vector<Item> items;
-    std::vector<LongRow> longrows;
-};
-HostPlan build_plan(const std::vector<int> &rowptr);
-
-// Assignment of the items to `grid` CTAs: CTA b takes the contiguous range
-// [part[b], part[b+1]); every CTA gets at least one item (grid <= items) and
-// the ranges have about equal cost (nonzeros + kItemCost per item).
-// lr_cta[l] holds the first and last CTA with a piece of long row l.
-struct HostPartition {
-    std::vector<int> part;
-    std::vector<int2> lr_cta;
-};
-HostPartition partition_items(const HostPlan &hp, int grid);
-
-// Device view of a CSR matrix with its plan.  pend (optional) splits each
-// row into two segments [rowptr[r], pend[r]) and [pend[r], rowptr[r+1]).
-template <class T>
-struct CsrDev {
-    int nrows = 0, ncols = 0;
-    const int *rowptr = nullptr;
-    const int *col = nullptr;
-    const T *val = nullptr;
-    const int *pend = nullptr;
-    const Item *items = nullptr;
-    int nitems = 0;
-    const LongRow *longrows = nullptr;
-    int *lr_count = nullptr;     // one ticket counter per long row (zeroed)
-    double *lr_part = nullptr;   // 2 partial sums per item
-    const int *part = nullptr;   // grid + 1 item boundaries (see partition_items)
-    const int2 *lr_cta = nullptr;  // first and last CTA of each long row
-    int *err = nullptr;          // device error flag (no kernel waits today; kept for bounded waits)
-};
+// Zeroed elements after the last nonzero of every matrix array the SpMV
+// kernels read: a warp's first and last 32-element steps may load up to 31
+// elements past its range (their products are discarded), and a zero
+// column index keeps the discarded lanes' gathers in bounds.
+constexpr int kSlack = 32;
 
 // ------------------------------------------------------------ status block
 
@@ -215,6 +151,7 @@ __device__ __forceinline__ double amax(double a, double b) {
 
 template <int NS, int NM>
 struct Red {
+    static constexpr int kNS = NS, kNM = NM;
     double s[NS > 0 ? NS : 1];
     double m[NM > 0 ? NM : 1];
     __device__ __forceinline__ void zero() {
@@ -310,7 +247,7 @@ __device__ __forceinline__ void grid_finish(Red<NS, NM> &red, double *partials, 
     fin(tot);
 }
 
-// ------------------------------------------------------ row-block SpMV core
+// ------------------------------------------------------- SpMV arithmetic
 
 // Exact float -> double by rebuilding the IEEE-754 fields (sign, exponent
 // rebiased from 127 to 1023, 23-bit significand shifted into the 52-bit
@@ -360,306 +297,6 @@ struct LaneSum<double, float> {
     __device__ __forceinline__ double value() const { return f2d_exact(s) + f2d_exact(c); }
 };
 
-// Row reduction of one block item with lane groups of G threads.  sprod
-// holds the item's products; epi.row(r, s1, s2, red) consumes each row.
-// With G = 1 every thread sums and finishes its own rows.  With G > 1 the
-// groups leave their row sums in rsum and the rows are then finished one
-// per thread, so that the epilogue (a chain of dependent loads, and in the
-// FP64 checks the expensive arithmetic) runs on all lanes instead of on one
-// lane per group; rows are taken in chunks of kThreads.  For FP64 sums the
-// G lane partials of a row go through shared memory (over the products,
-// once they are read) and one thread adds them in lane order: one FP64 add
-// per partial instead of log2(G) shuffle rounds on every lane, the FP64
-// pipe being narrow on this GPU.
-template <int G, bool SPLIT, class Acc, class T, class Epi, class RedT>
-__device__ __forceinline__ void reduce_rows(const CsrDev<T> &M, const Item &it, T *sprod, Epi &epi,
-                                            RedT &red, Acc (*rsum)[kThreads]) {
-    const int lane_g = threadIdx.x & (G - 1);
-    const int grp = threadIdx.x / G;
-    constexpr int ngrp = kThreads / G;
-    constexpr int kParts = SPLIT ? 2 : 1;
-    const int R = it.r1 - it.r0;
-    // transposed FP64 reduction when every partial of the item fits over the
-    // products (kCap * sizeof(T) bytes)
-    constexpr bool kFp64 = sizeof(Acc) == 8 && G > 1;
-    constexpr int kRounds = kFp64 ? 4 : 1;  // lane-group rounds kept in registers
-    const int nb = (R + ngrp - 1) / ngrp;
-    const bool transposed =
-        kFp64 && nb <= kRounds && R * G * kParts * (int)sizeof(Acc) <= kCap * (int)sizeof(T);
-    if (transposed) {
-        LaneSum<Acc, T> p1[kRounds], p2[kRounds];
-#pragma unroll
-        for (int b = 0; b < kRounds; ++b) {
-            const int lr = b * ngrp + grp;
-            if (b < nb && lr < R) {
-                const int r = it.r0 + lr;
-                const int a = __ldg(M.rowptr + r) - it.k0;
-                const int e1 = __ldg(M.rowptr + r + 1) - it.k0;
-                if (SPLIT) {
-                    const int sp = __ldg(M.pend + r) - it.k0;
-                    for (int e = a + lane_g; e < e1; e += G) {
-                        if (e < sp) p1[b].add(sprod[e]); else p2[b].add(sprod[e]);
-                    }
-                } else {
-                    for (int e = a + lane_g; e < e1; e += G) p1[b].add(sprod[e]);
-                }
-            }
-        }
-        __syncthreads();  // every product read: the buffer takes the partials
-        Acc *lp = reinterpret_cast<Acc *>(sprod);
-#pragma unroll
-        for (int b = 0; b < kRounds; ++b) {
-            const int lr = b * ngrp + grp;
-            if (b < nb && lr < R) {
-                lp[lr * G + lane_g] = p1[b].value();
-                if (SPLIT) lp[R * G + lr * G + lane_g] = p2[b].value();
-            }
-        }
-        __syncthreads();
-        for (int t = threadIdx.x; t < R; t += kThreads) {
-            Acc s1 = Acc(0), s2 = Acc(0);
-#pragma unroll
-            for (int g = 0; g < G; ++g) {
-                s1 += lp[t * G + g];
-                if (SPLIT) s2 += lp[R * G + t * G + g];
-            }
-            epi.row(it.r0 + t, s1, s2, red);
-        }
-        return;
-    }
-    for (int c0 = 0; c0 < R; c0 += (G > 1 ? kThreads : R)) {
-        const int cn = G > 1 ? min(kThreads, R - c0) : R;
-        for (int base = 0; base < cn; base += ngrp) {
-            const int lr = base + grp;
-            const int r = it.r0 + c0 + lr;
-            const bool active = lr < cn;
-            Acc s1 = Acc(0), s2 = Acc(0);
-            if (active) {
-                const int a = __ldg(M.rowptr + r) - it.k0;
-                const int b = __ldg(M.rowptr + r + 1) - it.k0;
-                if (SPLIT) {
-                    const int sp = __ldg(M.pend + r) - it.k0;
-                    for (int e = a + lane_g; e < b; e += G) {
-                        if (e < sp) s1 += to_acc<Acc>(sprod[e]); else s2 += to_acc<Acc>(sprod[e]);
-                    }
-                } else {
-                    for (int e = a + lane_g; e < b; e += G) s1 += to_acc<Acc>(sprod[e]);
-                }
-            }
-            if (G > 1) {
-#pragma unroll
-                for (int o = G / 2; o > 0; o >>= 1) {
-                    s1 += __shfl_down_sync(0xffffffffu, s1, o, G);
-                    if (SPLIT) s2 += __shfl_down_sync(0xffffffffu, s2, o, G);
-                }
-                if (active && lane_g == 0) {
-                    rsum[0][lr] = s1;
-                    if (SPLIT) rsum[1][lr] = s2;
-                }
-            } else if (active) {
-                epi.row(r, s1, s2, red);
-            }
-        }
-        if (G > 1) {
-            __syncthreads();
-            if ((int)threadIdx.x < cn)
-                epi.row(it.r0 + c0 + threadIdx.x, rsum[0][threadIdx.x], SPLIT ? rsum[1][threadIdx.x] : Acc(0), red);
-            if (c0 + kThreads < R) __syncthreads();  // rsum is refilled by the next chunk
-        }
-    }
-}
-
-// Whether a row-block kernel double-buffers its products and row sums (no
-// closing barrier per item).  Not for FP64 sums of split rows, whose row-sum
-// buffers are the largest and where the extra shared memory measured slower.
-template <class Acc, bool SPLIT>
-constexpr bool rowblock_double_buffered() {
-    return !(SPLIT && sizeof(Acc) == 8);
-}
-
-// Dynamic shared memory of a row-block kernel: the products of one item
-// (two when double-buffered), kept in the working precision; rows
-// accumulate them in Acc.
-template <class T, class Acc, bool SPLIT = false>
-constexpr size_t rowblock_smem() {
-    return (rowblock_double_buffered<Acc, SPLIT>() ? 2 : 1) * (size_t)kCap * sizeof(T);
-}
-
-// Load the value/column range of an item into registers (streaming loads:
-// evict-first, so that L1 keeps the gathered vector).
-template <class T>
-__device__ __forceinline__ void load_item(const CsrDev<T> &M, const Item &it, T (&v)[kPerThread], int (&c)[kPerThread]) {
-    const int nnz = it.k1 - it.k0;
-#pragma unroll
-    for (int u = 0; u < kPerThread; ++u) {
-        const int e = u * kThreads + threadIdx.x;
-        if (e < nnz) {
-            v[u] = __ldcs(M.val + it.k0 + e);
-            c[u] = __ldcs(M.col + it.k0 + e);
-        }
-    }
-}
-
-// Long-row ends pending in a CTA before they are finished together.
-constexpr int kRowBatch = 32;
-
-// Finish the pending long-row ends of a CTA, one per thread: add the warp
-// partials in warp order, then either consume the row (all its pieces in
-// this CTA) or publish this CTA's partial and, if this CTA is the last of
-// the row's CTAs to arrive, add every CTA's partial in CTA order and
-// consume the row.  Called by every thread of the CTA (it synchronises).
-template <class Acc, class T, class Epi, class RedT>
-__device__ __forceinline__ void finish_long_rows(const CsrDev<T> &M, int i0, int nq, const int *qlr,
-                                                 Acc (*qsum)[2][kWarps], Epi &epi, RedT &red) {
-    __syncthreads();
-    if ((int)threadIdx.x < nq) {
-        const int q = threadIdx.x;
-        double a1 = 0.0, a2 = 0.0;
-        for (int w = 0; w < kWarps; ++w) {
-            a1 += (double)qsum[q][0][w];
-            a2 += (double)qsum[q][1][w];
-        }
-        const int lr = qlr[q];
-        const LongRow L = M.longrows[lr];
-        const int row = M.items[L.first_item].r0;
-        const int first = L.first_item;
-        const int2 cr = M.lr_cta[lr];  // CTAs holding pieces of the row
-        if (cr.x == cr.y) {
-            epi.row(row, Acc(a1), Acc(a2), red);
-        } else {
-            const int slot = max(first, i0);  // this CTA's first piece of the row
-            M.lr_part[2 * (size_t)slot] = a1;
-            M.lr_part[2 * (size_t)slot + 1] = a2;
-            __threadfence();
-            const int t = atomicAdd(M.lr_count + lr, 1);
-            if (t == cr.y - cr.x) {
-                __threadfence();
-                double t1 = 0.0, t2 = 0.0;
-                for (int cc = cr.x; cc <= cr.y; ++cc) {
-                    const int sl = max(first, M.part[cc]);
-                    t1 += __ldcg(M.lr_part + 2 * (size_t)sl);
-                    t2 += __ldcg(M.lr_part + 2 * (size_t)sl + 1);
-                }
-                M.lr_count[lr] = 0;
-                epi.row(row, Acc(t1), Acc(t2), red);
-            }
-        }
-    }
-    __syncthreads();
-}
-
-// Process the contiguous range of items assigned to this CTA.  Each step
-// prefetches the next item's values and columns into registers, then
-// multiplies the current item by the gathered vector in the working
-// precision (into shared memory) and reduces its rows with lane groups sized
-// to the mean row length, accumulating in Acc (FP64 for the termination
-// check: FP32 products summed in FP64).
-// Consecutive pieces of a long row accumulate per thread; at the row's end
-// (in this CTA) the warps leave their partials in shared memory and up to
-// kRowBatch such row ends are finished together (finish_long_rows); a long
-// row that crosses a CTA boundary is combined by the last of its
-// contributors, in CTA order.  gather(c) returns the vector entry for
-// column c in the accumulation type; epi.row(r, s1, s2, red) consumes rows.
-template <class Acc, bool SPLIT, class T, class Gather, class Epi, class RedT>
-__device__ __forceinline__ bool run_items(const CsrDev<T> &M, const Gather &gather, Epi &epi, RedT &red) {
-    // Products and row sums are double-buffered by item parity: item i+1
-    // writes the other buffers while slow threads may still read item i's, and
-    // the barrier after item i+1's products orders item i's reads before item
-    // i+2 reuses them, so an item needs no closing barrier.  Single-buffered
-    // kernels close every item with a barrier instead.
-    constexpr bool kDB = rowblock_double_buffered<Acc, SPLIT>();
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sprod_buf = reinterpret_cast<T *>(smem_raw);
-    __shared__ Acc rsum_buf[kDB ? 2 : 1][SPLIT ? 2 : 1][kThreads];
-    __shared__ Acc qsum[kRowBatch][2][kWarps];
-    __shared__ int qlr[kRowBatch];
-    const int i0 = M.part[blockIdx.x];
-    const int i1 = M.part[blockIdx.x + 1];
-    T va[kPerThread], vb[kPerThread];
-    int ca[kPerThread], cb[kPerThread];
-    // descriptors run one item ahead of the value/column registers
-    Item cur, nx;
-    if (i0 < i1) {
-        cur = M.items[i0];
-        load_item(M, cur, va, ca);
-    }
-    if (i0 + 1 < i1) nx = M.items[i0 + 1];
-    LaneSum<Acc, T> ps1, ps2;  // running sums of a long row's pieces
-    int nq = 0;                      // pending long-row ends (uniform in the CTA)
-    for (int itx = i0; itx < i1; ++itx) {
-        const Item it = cur;
-        const bool has_next = itx + 1 < i1;
-        Item nx2;
-        if (has_next) {
-            load_item(M, nx, vb, cb);
-            if (itx + 2 < i1) nx2 = M.items[itx + 2];
-        }
-        const int nnz = it.k1 - it.k0;
-        if (it.r1 >= 0) {
-            const int buf = kDB ? ((itx - i0) & 1) : 0;
-            T *sprod = sprod_buf + buf * kCap;
-            Acc(*rsum)[kThreads] = rsum_buf[buf];
-#pragma unroll
-            for (int u = 0; u < kPerThread; ++u) {
-                const int e = u * kThreads + threadIdx.x;
-                if (e < nnz) sprod[e] = va[u] * gather(ca[u]);
-            }
-            __syncthreads();
-            const int R = it.r1 - it.r0;
-            const int avg = R > 0 ? nnz / R : 0;
-            if (avg >= 24) reduce_rows<32, SPLIT, Acc>(M, it, sprod, epi, red, rsum);
-            else if (avg >= 12) reduce_rows<16, SPLIT, Acc>(M, it, sprod, epi, red, rsum);
-            else if (avg >= 6) reduce_rows<8, SPLIT, Acc>(M, it, sprod, epi, red, rsum);
-            else if (avg >= 3) reduce_rows<4, SPLIT, Acc>(M, it, sprod, epi, red, rsum);
-            else reduce_rows<1, SPLIT, Acc>(M, it, sprod, epi, red, rsum);
-            if (!kDB) __syncthreads();
-        } else {
-            const int row = it.r0;
-            const int sp = SPLIT ? __ldg(M.pend + row) - it.k0 : 0x7fffffff;
-#pragma unroll
-            for (int u = 0; u < kPerThread; ++u) {
-                const int e = u * kThreads + threadIdx.x;
-                if (e < nnz) {
-                    const T pr = va[u] * gather(ca[u]);
-                    if (!SPLIT || e < sp) ps1.add(pr); else ps2.add(pr);
-                }
-            }
-            const bool row_end = !has_next || nx.r1 != it.r1;
-            if (row_end) {
-                Acc s1 = ps1.value(), s2 = ps2.value();
-                ps1 = LaneSum<Acc, T>();
-                ps2 = LaneSum<Acc, T>();
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    s1 += __shfl_down_sync(0xffffffffu, s1, o);
-                    s2 += __shfl_down_sync(0xffffffffu, s2, o);
-                }
-                const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-                if (lane == 0) {
-                    qsum[nq][0][warp] = s1;
-                    qsum[nq][1][warp] = s2;
-                }
-                if (threadIdx.x == 0) qlr[nq] = -(it.r1 + 1);
-                if (++nq == kRowBatch) {
-                    finish_long_rows<Acc>(M, i0, nq, qlr, qsum, epi, red);
-                    nq = 0;
-                }
-            }
-        }
-        if (has_next) {
-#pragma unroll
-            for (int u = 0; u < kPerThread; ++u) {
-                va[u] = vb[u];
-                ca[u] = cb[u];
-            }
-            cur = nx;
-            nx = nx2;
-        }
-    }
-    if (nq > 0) finish_long_rows<Acc>(M, i0, nq, qlr, qsum, epi, red);
-    return true;
-}
-
 // ------------------------------------------------------------- utilities
 
 // Kernel launches issued by this host thread (for the launch count the
@@ -689,7 +326,6 @@ inline void launch(void (*kern)(KArgs...), int grid, int block, cudaStream_t str
 __host__ __device__ __forceinline__ int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 int device_sm_count();
-int grid_for_items(int nitems, const void *kernel, int smem_dynamic = 0);
 int grid_for_n(long long n, int threads = kThreads);
 
 }  // namespace gb

@@ -51,6 +51,7 @@
 
 #include "common.cuh"
 #include "engine.cuh"
+#include "spmv.cuh"
 #include "policy.cuh"
 
 namespace gb {
@@ -91,6 +92,10 @@ struct Vecs {
 #define GB_MIN_BLOCKS 4
 #endif
 constexpr int kMinBlocks = GB_MIN_BLOCKS;
+// steps of 32 nonzeros per batch of the warp-stream SpMV (see spmv.cuh)
+constexpr int kU = 4;
+// rows longer than this go to CTA bundles in the warp-stream plan
+constexpr int kBundleMin = 4096;
 
 template <class T>
 __device__ __forceinline__ T clampv(T v, T lo, T hi) {
@@ -192,12 +197,12 @@ struct EpiInit {
 };
 
 template <class T>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : 2) k_pcg_init(CsrDev<T> PAt, Vecs<T> v, Status *st, double *partials,
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : 2) k_pcg_init(CsrW<T> PAt, Vecs<T> v, Status *st, double *partials,
                                                        cudaGraphConditionalHandle hP, int use_h) {
     EpiInit<T> epi{v, T(st->sigma)};
     Red<1, 1> red;
     red.zero();
-    run_items<T, false>(PAt, GatherVec<T, T>{v.xt}, epi, red);
+    warp_rows<kU, T, false>(PAt, GatherVec<T, T>{v.xt}, epi, red);
     auto fin = [&](const Red<1, 1> &t) {
         if (threadIdx.x != 0) return;
         st->ry = t.s[0];
@@ -209,7 +214,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : 2) k_p
         st->pcg_continue = cont;
         if (use_h) cudaGraphSetConditional(hP, cont);
     };
-    grid_finish<1, 1>(red, partials, &st->tickets[kTkI1], fin);
+    grid_finish_w<1, 1>(red, PAt, partials, &st->tickets[kTkI1], fin);
 }
 
 // p = -yv + beta p_prev (stored in pt[0..n)), t = rho A p (pt[n..n+m))
@@ -222,7 +227,7 @@ struct EpiDir {
 };
 
 template <class T>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : 2) k_pcg_p_t(CsrDev<T> A, Vecs<T> v, const Status *st) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : 2) k_pcg_p_t(CsrW<T> A, Vecs<T> v, const Status *st) {
     const T beta = T(st->beta);
     const int n = v.n;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -231,7 +236,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : 2) k_p
     }
     EpiDir<T> epi{v.pt + n, v.rs, T(st->rho)};
     Red<0, 0> red;
-    run_items<T, false>(A, GatherDir<T>{v.ypc, beta}, epi, red);
+    warp_rows<kU, T, false>(A, GatherDir<T>{v.ypc, beta}, epi, red);
 }
 
 // Kp = P p + sigma p + A' t;  p'Kp
@@ -248,11 +253,11 @@ struct EpiKp {
 };
 
 template <class T>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : 2) k_pcg_kp(CsrDev<T> PAt, Vecs<T> v, Status *st, double *partials) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : 2) k_pcg_kp(CsrW<T> PAt, Vecs<T> v, Status *st, double *partials) {
     EpiKp<T> epi{v, T(st->sigma)};
     Red<1, 0> red;
     red.zero();
-    run_items<T, false>(PAt, GatherVec<T, T>{v.pt}, epi, red);
+    warp_rows<kU, T, false>(PAt, GatherVec<T, T>{v.pt}, epi, red);
     auto fin = [&](const Red<1, 0> &t) {
         if (threadIdx.x != 0) return;
         const double pkp = t.s[0];
@@ -264,7 +269,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : 2) k_p
             st->breakdown = 1;
         }
     };
-    grid_finish<1, 0>(red, partials, &st->tickets[kTkK2], fin);
+    grid_finish_w<1, 0>(red, PAt, partials, &st->tickets[kTkK2], fin);
 }
 
 // x~ += a p; r += a Kp; yv = M^{-1} r; p_prev = p; r'yv; ||r||_inf; beta.
@@ -333,7 +338,7 @@ struct EpiAdmm {
 };
 
 template <class T>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : 2) k_admm_update(CsrDev<T> A, Vecs<T> v, Status *st) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : 2) k_admm_update(CsrW<T> A, Vecs<T> v, Status *st) {
     const T alpha = T(st->alpha);
     const T rho = T(st->rho);
     const int n = v.n;
@@ -345,7 +350,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : 2) k_a
     }
     EpiAdmm<T> epi{v, alpha, rho, T(1.0 / st->rho)};
     Red<0, 0> red;
-    run_items<T, false>(A, GatherVec<T, T>{v.xt}, epi, red);
+    warp_rows<kU, T, false>(A, GatherVec<T, T>{v.xt}, epi, red);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->k += 1;
         st->cg_since_update += st->cg_it;
@@ -371,16 +376,16 @@ struct EpiCheckA {
 };
 
 template <class T>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_check_a(CsrDev<T> A, Vecs<T> v, Status *st, double *partials) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_check_a(CsrW<T> A, Vecs<T> v, Status *st, double *partials) {
     EpiCheckA<T> epi{v};
     Red<0, 6> red;
     red.zero();
-    run_items<double, false>(A, GatherVec<T, T>{v.xy}, epi, red);
+    warp_rows<kU, double, false>(A, GatherVec<T, T>{v.xy}, epi, red);
     auto fin = [&](const Red<0, 6> &t) {
         if (threadIdx.x == 0)
             for (int i = 0; i < 6; ++i) st->c1[i] = t.m[i];
     };
-    grid_finish<0, 6>(red, partials, &st->tickets[kTkC1], fin);
+    grid_finish_w<0, 6>(red, A, partials, &st->tickets[kTkC1], fin);
 }
 
 // Infeasibility detection (Section 3.1), part A (rows of A), on the
@@ -411,11 +416,11 @@ struct EpiInfA {
 };
 
 template <class T>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_inf_a(CsrDev<T> A, Vecs<T> v, Status *st, double *partials) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_inf_a(CsrW<T> A, Vecs<T> v, Status *st, double *partials) {
     EpiInfA<T> epi{v};
     Red<1, 3> red;
     red.zero();
-    run_items<T, false>(A, GatherVec<T, T>{v.dxy}, epi, red);
+    warp_rows<kU, T, false>(A, GatherVec<T, T>{v.dxy}, epi, red);
     auto fin = [&](const Red<1, 3> &t) {
         if (threadIdx.x != 0) return;
         st->inf_a[0] = t.m[0];
@@ -423,7 +428,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_inf_a(CsrD
         st->inf_a[2] = t.m[2];
         st->inf_a[3] = t.s[0];
     };
-    grid_finish<1, 3>(red, partials, &st->tickets[kTkInfA], fin);
+    grid_finish_w<1, 3>(red, A, partials, &st->tickets[kTkInfA], fin);
 }
 
 // Part B (rows of [P A']): ||D^-1 P_bar dx_bar|| and ||D^-1 A_bar' dy_bar||
@@ -443,11 +448,11 @@ struct EpiInfB {
 };
 
 template <class T>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_inf_b(CsrDev<T> PAt, Vecs<T> v, Status *st, double *partials) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_inf_b(CsrW<T> PAt, Vecs<T> v, Status *st, double *partials) {
     EpiInfB<T> epi{v};
     Red<1, 3> red;
     red.zero();
-    run_items<T, true>(PAt, GatherVec<T, T>{v.dxy}, epi, red);
+    warp_rows<kU, T, true>(PAt, GatherVec<T, T>{v.dxy}, epi, red);
     auto fin = [&](const Red<1, 3> &t) {
         if (threadIdx.x != 0) return;
         st->inf_b[0] = t.m[0];
@@ -455,7 +460,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_inf_b(CsrD
         st->inf_b[2] = t.s[0];
         st->inf_b[3] = t.m[2];
     };
-    grid_finish<1, 3>(red, partials, &st->tickets[kTkInfB], fin);
+    grid_finish_w<1, 3>(red, PAt, partials, &st->tickets[kTkInfB], fin);
 }
 
 // The approximate certificate tests of Section 3.1 on the normalised
@@ -501,14 +506,14 @@ struct EpiCheckB {
 };
 
 template <class T>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_check_b(CsrDev<T> PAt, Vecs<T> v, Status *st, double *partials,
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_check_b(CsrW<T> PAt, Vecs<T> v, Status *st, double *partials,
                                                       PolicyDev pol, cudaGraphConditionalHandle hA, int use_h) {
     __shared__ double new_rho_sh;
     __shared__ int decide_sh;
     EpiCheckB<T> epi{v};
     Red<1, 6> red;
     red.zero();
-    run_items<double, true>(PAt, GatherVec<T, T>{v.xy}, epi, red);
+    warp_rows<kU, double, true>(PAt, GatherVec<T, T>{v.xy}, epi, red);
     auto fin = [&](const Red<1, 6> &t) {
         if (threadIdx.x == 0) {
             const double cinv = st->cinv;
@@ -563,7 +568,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_check_b(Cs
             if (use_h) cudaGraphSetConditional(hA, st->admm_continue);
         }
     };
-    grid_finish<1, 6>(red, partials, &st->tickets[kTkC2], fin);
+    grid_finish_w<1, 6>(red, PAt, partials, &st->tickets[kTkC2], fin);
 }
 
 template <class T>
@@ -610,17 +615,17 @@ struct EpiStore {
 };
 
 template <class T, class Acc>
-__global__ void __launch_bounds__(kThreads) k_spmv(CsrDev<T> M, const T *x, T *y, Acc alpha) {
+__global__ void __launch_bounds__(kThreads) k_spmv(CsrW<T> M, const T *x, T *y, Acc alpha) {
     EpiStore<T, Acc> epi{y, alpha};
     Red<0, 0> red;
-    run_items<Acc, false>(M, GatherVec<T, Acc>{x}, epi, red);
+    warp_rows<kU, Acc, false>(M, GatherVec<T, Acc>{x}, epi, red);
 }
 
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_spmv_dbl(CsrDev<T> M, const T *x, double *y) {
+__global__ void __launch_bounds__(kThreads) k_spmv_dbl(CsrW<T> M, const T *x, double *y) {
     EpiStore<double, double> epi{y, 1.0};
     Red<0, 0> red;
-    run_items<double, false>(M, GatherVec<T, T>{x}, epi, red);
+    warp_rows<kU, double, false>(M, GatherVec<T, T>{x}, epi, red);
 }
 
 // t0 = rho (zt - z) + y
@@ -811,9 +816,9 @@ public:
         PAt_val_ = convert(std::move(sd.PAt_val), nnzPAt);
         D_ = std::move(sd.D);
         E_ = std::move(sd.E);
-        // plans
-        build_plan_dev(sd.A_rowptr_host, planA_);
-        build_plan_dev(sd.PAt_rowptr_host, planPAt_);
+        // host row pointers of the work plans
+        matA_.rp = std::move(sd.A_rowptr_host);
+        matPAt_.rp = std::move(sd.PAt_rowptr_host);
         // vectors
         const size_t nm = (size_t)n + m;
         xy_.alloc(sizeof(T) * std::max<size_t>(nm, 1));
@@ -844,34 +849,25 @@ public:
         GB_CUDA(cudaMemsetAsync(x_out_.p, 0, x_out_.bytes, stream_));
         GB_CUDA(cudaMemsetAsync(y_out_.p, 0, y_out_.bytes, stream_));
         GB_CUDA(cudaMemsetAsync(z_out_.p, 0, z_out_.bytes, stream_));
-        // launch geometry and reduction scratch
-        // dynamic shared memory of the pipelined row-block kernels
-        for (const void *k : {(const void *)k_pcg_p_t<T>, (const void *)k_pcg_kp<T>, (const void *)k_pcg_init<T>,
-                              (const void *)k_admm_update<T>, (const void *)k_spmv<T, T>, (const void *)k_inf_a<T>,
-                              (const void *)k_inf_b<T>})
-            GB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemT));
-        for (const void *k : {(const void *)k_check_a<T>, (const void *)k_spmv_dbl<T>})
-            GB_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemD));
-        GB_CUDA(cudaFuncSetAttribute((const void *)k_check_b<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kSmemDS));
-        // each kernel's grid: its items, capped at the CTAs that fit at once
-        gPt_ = grid_for_items(planA_.nitems, (const void *)k_pcg_p_t<T>, kSmemT);
-        gAdmm_ = grid_for_items(planA_.nitems, (const void *)k_admm_update<T>, kSmemT);
-        gCa_ = grid_for_items(planA_.nitems, (const void *)k_check_a<T>, kSmemD);
-        gKp_ = grid_for_items(planPAt_.nitems, (const void *)k_pcg_kp<T>, kSmemT);
-        gInit_ = grid_for_items(planPAt_.nitems, (const void *)k_pcg_init<T>, kSmemT);
-        gCb_ = grid_for_items(planPAt_.nitems, (const void *)k_check_b<T>, kSmemDS);
-        gIa_ = grid_for_items(planA_.nitems, (const void *)k_inf_a<T>, kSmemT);
-        gIb_ = grid_for_items(planPAt_.nitems, (const void *)k_inf_b<T>, kSmemT);
+        // launch geometry and reduction scratch: each matrix kernel's grid
+        // is the CTAs that fit at once, fewer for small matrices
+        gPt_ = grid_for_rows(matA_.rp, (const void *)k_pcg_p_t<T>);
+        gAdmm_ = grid_for_rows(matA_.rp, (const void *)k_admm_update<T>);
+        gCa_ = grid_for_rows(matA_.rp, (const void *)k_check_a<T>);
+        gKp_ = grid_for_rows(matPAt_.rp, (const void *)k_pcg_kp<T>);
+        gInit_ = grid_for_rows(matPAt_.rp, (const void *)k_pcg_init<T>);
+        gCb_ = grid_for_rows(matPAt_.rp, (const void *)k_check_b<T>);
+        gIa_ = grid_for_rows(matA_.rp, (const void *)k_inf_a<T>);
+        gIb_ = grid_for_rows(matPAt_.rp, (const void *)k_inf_b<T>);
         // vector kernels: about 4 elements per thread
         const int cap = device_sm_count() * 8;
         gridVec_ = std::max(1, std::min(grid_for_n(n, kThreads), cap));
         gridN_ = std::max(1, std::min(grid_for_n(std::max(n, m), kThreads * 4), cap));
         const int maxgrid = std::max({gPt_, gAdmm_, gCa_, gKp_, gInit_, gCb_, gIa_, gIb_, gridN_, gridVec_});
-        const int gSpA = grid_for_items(planA_.nitems, (const void *)k_spmv<T, T>, kSmemT);
-        const int gSpP = grid_for_items(planPAt_.nitems, (const void *)k_spmv<T, T>, kSmemT);
-        for (int g : {gPt_, gAdmm_, gCa_, gIa_, gSpA}) part_for(planA_, g);
-        for (int g : {gKp_, gInit_, gCb_, gIb_, gSpP}) part_for(planPAt_, g);
+        const int gSpA = grid_for_rows(matA_.rp, (const void *)k_spmv<T, T>);
+        const int gSpP = grid_for_rows(matPAt_.rp, (const void *)k_spmv<T, T>);
+        for (int g : {gPt_, gAdmm_, gCa_, gIa_, gSpA}) plan_for(matA_, g);
+        for (int g : {gKp_, gInit_, gCb_, gIb_, gSpP}) plan_for(matPAt_, g);
         partials_.alloc(sizeof(double) * (size_t)maxgrid * 8);
         // status block
         Status h;
@@ -985,7 +981,7 @@ public:
         Status h = read_status();
         Vecs<T> v = vecs();
         launch(k_warm<T>, gridN_, kThreads, stream_, v, xd.as<double>(), yd.as<double>(), c_);
-        spmv_dev(planA_, A_val_.as<T>(), v.xt, v.zt, T(1));
+        spmv_dev(matA_, A_val_.as<T>(), v.xt, v.zt, T(1));
         launch(k_proj_z<T>, ceil_div(std::max(m, 1), 256), 256, stream_, v);
         launch(k_t0<T>, ceil_div(std::max(m, 1), 256), 256, stream_, v, h.rho0);
         const int one = 1;
@@ -1113,13 +1109,13 @@ public:
             yd(sizeof(double) * std::max(nout, 1));
         if (nin) GB_CUDA(cudaMemcpyAsync(xd.p, x, sizeof(double) * nin, cudaMemcpyHostToDevice, stream_));
         launch(k_from_double<T>, ceil_div(std::max(nin, 1), 256), 256, stream_, xd.as<double>(), xT.as<T>(), nin);
-        const DevPlan &pl = isA ? planA_ : planPAt_;
+        const MatPlans &pl = isA ? matA_ : matPAt_;
         const T *val = isA ? A_val_.as<T>() : PAt_val_.as<T>();
         if (fp64acc) {
             // FP64 output through a double staging vector
             DevBuf yy(sizeof(double) * std::max(nout, 1));
-            const int g = grid_for_items(pl.nitems, (const void *)k_spmv_dbl<T>, kSmemD);
-            CsrDev<T> M = csr(pl, val, g);
+            const int g = grid_for_rows(pl.rp, (const void *)k_spmv_dbl<T>);
+            CsrW<T> M = csr(pl, val, g);
             k_spmv_d(M, xT.as<T>(), yy.as<double>(), g);
             GB_CUDA(cudaMemcpyAsync(y, yy.p, sizeof(double) * nout, cudaMemcpyDeviceToHost, stream_));
         } else {
@@ -1152,7 +1148,7 @@ public:
         v.minv = minv.as<T>();
         v.zt = zt.as<T>();
         v.z = zz.as<T>();
-        spmv_dev(planA_, A_val_.as<T>(), v.xt, v.zt, T(1));
+        spmv_dev(matA_, A_val_.as<T>(), v.xt, v.zt, T(1));
         launch(k_t0<T>, ceil_div(std::max(m, 1), 256), 256, stream_, v, rho);
         launch(k_minv<T>, ceil_div(std::max(n, 1), 256), 256, stream_, v, rho, s_.sigma);
         // private status: parameters of the main one, with rho and eps set
@@ -1184,7 +1180,7 @@ public:
         upload(y, v.xy + n, m);
         upload(z, v.z, m);
         upload(xt, v.xt, n);
-        spmv_dev(planA_, A_val_.as<T>(), v.xt, v.zt, T(1));
+        spmv_dev(matA_, A_val_.as<T>(), v.xt, v.zt, T(1));
         launch(k_t0<T>, ceil_div(std::max(m, 1), 256), 256, stream_, v, rho);
         launch(k_minv<T>, ceil_div(std::max(n, 1), 256), 256, stream_, v, rho, s_.sigma);
         Status h = read_status();
@@ -1340,99 +1336,114 @@ public:
         GB_CUDA(cudaStreamSynchronize(stream_));
     }
 
-    void spmv_noalloc(int which, const void *x, void *y, double *part, int *count, long long max_items,
-                      long long max_long_rows) override {
+    void spmv_noalloc(int which, const void *x, void *y, unsigned char *scratch, size_t scratch_bytes) override {
         const bool isA = which == GBOSQP_MAT_A;
-        const DevPlan &pl = isA ? planA_ : planPAt_;
-        if (pl.nitems > max_items || pl.nlong > max_long_rows)
-            fail(GBOSQP_ERR_UNSUPPORTED, "matrix needs " + std::to_string(pl.nitems) + " work items and " +
-                                             std::to_string(pl.nlong) + " long rows; the allocation-free SpMV holds at most " +
-                                             std::to_string(max_items) + " and " + std::to_string(max_long_rows));
-        const int g = grid_for_items(pl.nitems, (const void *)k_spmv<T, T>, kSmemT);
-        CsrDev<T> M = csr(pl, isA ? A_val_.as<T>() : PAt_val_.as<T>(), g);  // partition built at set-up
-        M.lr_part = part;
-        M.lr_count = count;
-        if (pl.nlong > 0) GB_CUDA(cudaMemsetAsync(count, 0, sizeof(int) * (size_t)pl.nlong, stream_));
-        launch_smem(k_spmv<T, T>, g, kThreads, kSmemT, stream_, M, static_cast<const T *>(x), static_cast<T *>(y), T(1));
+        const MatPlans &mp = isA ? matA_ : matPAt_;
+        const int g = grid_for_rows(mp.rp, (const void *)k_spmv<T, T>);
+        // the plan for this grid was built at set-up; a missing one is an
+        // internal error here (building it would allocate)
+        auto it = mp.by_grid.find(g);
+        if (it == mp.by_grid.end()) fail(GBOSQP_ERR_CUDA, "internal: no SpMV plan for the allocation-free grid");
+        const WDev &pd = it->second;
+        if (pd.scratch_bytes > scratch_bytes)
+            fail(GBOSQP_ERR_UNSUPPORTED, "the matrix's SpMV plan needs " + std::to_string(pd.scratch_bytes) +
+                                             " bytes of scratch; the allocation-free SpMV holds " +
+                                             std::to_string(scratch_bytes));
+        CsrW<T> M = csr(mp, isA ? A_val_.as<T>() : PAt_val_.as<T>(), g);
+        // the same layout as the plan's own scratch, in the caller's memory
+        M.split_count = reinterpret_cast<int *>(scratch);
+        M.split_part = reinterpret_cast<double *>(scratch + pd.off_part);
+        M.split_red = reinterpret_cast<double *>(scratch + pd.off_red);
+        GB_CUDA(cudaMemsetAsync(scratch, 0, pd.off_part, stream_));  // the tickets start at zero
+        launch(k_spmv<T, T>, g, kThreads, stream_, M, static_cast<const T *>(x), static_cast<T *>(y), T(1));
     }
 
 private:
-    struct PartDev {
-        DevBuf part, lr_cta;
+    // Warp-stream plan of one matrix for one grid size: the immutable
+    // tables (items, per-warp ranges and split rows) and the zeroed scratch
+    // of the split rows (tickets, partial sums, epilogue sums).
+    struct WDev {
+        DevBuf meta, scratch;
+        int nwarps = 0, nsplit = 0;
+        size_t off_wpart = 0, off_wsplit = 0, off_split = 0;  // in meta
+        size_t off_part = 0, off_red = 0, scratch_bytes = 0;  // in scratch
     };
-    struct DevPlan {
-        DevBuf items, longrows, count, part;
-        HostPlan host;
-        mutable std::map<int, PartDev> parts;  // by grid size
-        int nitems = 0;
-        int nrows = 0;
-        int nlong = 0;
+    struct MatPlans {
+        std::vector<int> rp;                     // host row pointers
+        mutable std::map<int, WDev> by_grid;     // plans by grid size
     };
 
     DevBuf convert(DevBuf &&src, long long count) {
         if (sizeof(T) == sizeof(double)) return std::move(src);
-        DevBuf out(sizeof(T) * (count + 8));  // 8 elements of slack past the last nonzero, like the set-up arrays
+        DevBuf out(sizeof(T) * (count + kSlack));  // zeroed slack past the last element, like the set-up arrays
+        GB_CUDA(cudaMemsetAsync(out.as<T>() + count, 0, sizeof(T) * kSlack, stream_));
         if (count) launch(k_from_double<T>, ceil_div(count, 256), 256, stream_, src.as<double>(), out.as<T>(), count);
         GB_CUDA(cudaGetLastError());
         return out;  // src is released after the conversion in stream order
     }
 
-    void build_plan_dev(const std::vector<int> &rp, DevPlan &pl) {
-        pl.host = build_plan(rp);
-        const HostPlan &hp = pl.host;
-        pl.nitems = (int)hp.items.size();
-        pl.nrows = (int)rp.size() - 1;
-        pl.nlong = (int)hp.longrows.size();
-        pl.items.alloc(sizeof(Item) * std::max<size_t>(hp.items.size(), 1));
-        pl.longrows.alloc(sizeof(LongRow) * std::max<size_t>(hp.longrows.size(), 1));
-        pl.count.alloc(sizeof(int) * std::max<size_t>(hp.longrows.size(), 1));
-        pl.part.alloc(sizeof(double) * 2 * std::max<size_t>(hp.items.size(), 1));
-        if (!hp.items.empty())
-            GB_CUDA(cudaMemcpyAsync(pl.items.p, hp.items.data(), sizeof(Item) * hp.items.size(), cudaMemcpyHostToDevice,
-                                    stream_));
-        if (!hp.longrows.empty())
-            GB_CUDA(cudaMemcpyAsync(pl.longrows.p, hp.longrows.data(), sizeof(LongRow) * hp.longrows.size(),
-                                    cudaMemcpyHostToDevice, stream_));
-        GB_CUDA(cudaMemsetAsync(pl.count.p, 0, pl.count.bytes, stream_));
-        GB_CUDA(cudaStreamSynchronize(stream_));
+    // The plan of matrix mp for a launch of `grid` CTAs (built once per
+    // grid size; kernels with the same grid share it).
+    const WDev &plan_for(const MatPlans &mp, int grid) const {
+        auto it = mp.by_grid.find(grid);
+        if (it != mp.by_grid.end()) return it->second;
+        WPlanCost cost;
+        cost.bundle_min = kBundleMin;
+        const WPlanHost hp = build_wplan(mp.rp, grid * kWWarps, cost);
+        WDev d;
+        d.nwarps = hp.nwarps;
+        d.nsplit = (int)hp.split.size();
+        auto up16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
+        d.off_wpart = up16(sizeof(WItem) * hp.items.size());
+        d.off_wsplit = d.off_wpart + up16(sizeof(int) * hp.wpart.size());
+        d.off_split = d.off_wsplit + up16(sizeof(WSplit) * hp.wsplit.size());
+        const size_t meta_bytes = d.off_split + up16(sizeof(SplitRow) * hp.split.size());
+        std::vector<unsigned char> h(meta_bytes, 0);
+        if (!hp.items.empty()) std::memcpy(h.data(), hp.items.data(), sizeof(WItem) * hp.items.size());
+        std::memcpy(h.data() + d.off_wpart, hp.wpart.data(), sizeof(int) * hp.wpart.size());
+        std::memcpy(h.data() + d.off_wsplit, hp.wsplit.data(), sizeof(WSplit) * hp.wsplit.size());
+        if (!hp.split.empty()) std::memcpy(h.data() + d.off_split, hp.split.data(), sizeof(SplitRow) * hp.split.size());
+        d.meta.alloc(meta_bytes);
+        // pageable source: the copy is staged before the call returns
+        GB_CUDA(cudaMemcpyAsync(d.meta.p, h.data(), meta_bytes, cudaMemcpyHostToDevice, stream_));
+        d.off_part = up16(sizeof(int) * hp.split.size());
+        d.off_red = d.off_part + up16(2 * sizeof(double) * (size_t)hp.nslots);
+        d.scratch_bytes = d.off_red + up16(kMaxSplitSums * sizeof(double) * hp.split.size());
+        d.scratch.alloc(d.scratch_bytes);
+        GB_CUDA(cudaMemsetAsync(d.scratch.p, 0, d.scratch.bytes, stream_));
+        return mp.by_grid.emplace(grid, std::move(d)).first->second;
     }
 
-    // item partition of a plan for a launch of `grid` CTAs (built once per
-    // grid size; kernels with the same grid share it)
-    const PartDev &part_for(const DevPlan &pl, int grid) const {
-        auto it = pl.parts.find(grid);
-        if (it != pl.parts.end()) return it->second;
-        HostPartition hp = partition_items(pl.host, grid);
-        PartDev d;
-        d.part.alloc(sizeof(int) * hp.part.size());
-        d.lr_cta.alloc(sizeof(int2) * std::max<size_t>(hp.lr_cta.size(), 1));
-        GB_CUDA(cudaMemcpyAsync(d.part.p, hp.part.data(), sizeof(int) * hp.part.size(), cudaMemcpyHostToDevice, stream_));
-        if (!hp.lr_cta.empty())
-            GB_CUDA(cudaMemcpyAsync(d.lr_cta.p, hp.lr_cta.data(), sizeof(int2) * hp.lr_cta.size(), cudaMemcpyHostToDevice,
-                                    stream_));
-        GB_CUDA(cudaStreamSynchronize(stream_));
-        return pl.parts.emplace(grid, std::move(d)).first->second;
-    }
-
-    CsrDev<T> csr(const DevPlan &pl, const T *val, int grid) const {
-        const bool isA = &pl == &planA_;
-        const PartDev &pd = part_for(pl, grid);
-        CsrDev<T> M;
-        M.part = pd.part.template as<int>();
-        M.lr_cta = pd.lr_cta.template as<int2>();
-        M.nrows = pl.nrows;
+    CsrW<T> csr(const MatPlans &mp, const T *val, int grid) const {
+        const bool isA = &mp == &matA_;
+        const WDev &pd = plan_for(mp, grid);
+        const unsigned char *meta = pd.meta.template as<unsigned char>();
+        unsigned char *scr = pd.scratch.template as<unsigned char>();
+        CsrW<T> M;
+        M.nrows = (int)mp.rp.size() - 1;
         M.ncols = isA ? n : n + m;
         M.rowptr = (isA ? A_rowptr_ : PAt_rowptr_).template as<int>();
         M.col = (isA ? A_col_ : PAt_col_).template as<int>();
         M.val = val;
         M.pend = isA ? nullptr : PAt_pend_.template as<int>();
-        M.items = pl.items.template as<Item>();
-        M.nitems = pl.nitems;
-        M.longrows = pl.longrows.template as<LongRow>();
-        M.lr_count = pl.count.template as<int>();
-        M.lr_part = pl.part.template as<double>();
-        M.err = &(st_.template as<Status>()->device_error);
+        M.items = reinterpret_cast<const WItem *>(meta);
+        M.wpart = reinterpret_cast<const int *>(meta + pd.off_wpart);
+        M.wsplit = reinterpret_cast<const WSplit *>(meta + pd.off_wsplit);
+        M.split = reinterpret_cast<const SplitRow *>(meta + pd.off_split);
+        M.nsplit = pd.nsplit;
+        M.split_count = reinterpret_cast<int *>(scr);
+        M.split_part = reinterpret_cast<double *>(scr + pd.off_part);
+        M.split_red = reinterpret_cast<double *>(scr + pd.off_red);
         return M;
+    }
+    // CTAs of a warp-stream kernel: as many as fit at once, fewer when the
+    // matrix is small (at least about 512 nonzeros per warp)
+    int grid_for_rows(const std::vector<int> &rp, const void *kernel) const {
+        int per_sm = 0;
+        GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0));
+        const long long work = (rp.empty() ? 0LL : (long long)rp.back()) + 16LL * (long long)(rp.size() - 1);
+        const long long want = (work + (long long)kWWarps * 512 - 1) / ((long long)kWWarps * 512);
+        return (int)std::max(1LL, std::min<long long>(want, (long long)device_sm_count() * std::max(per_sm, 1)));
     }
     // rs from the scaled bounds, and the weighted column sums it implies
     void rho_vector_setup() {
@@ -1444,8 +1455,8 @@ private:
         GB_CUDA(cudaGetLastError());
     }
 
-    CsrDev<T> csrA(int grid) const { return csr(planA_, A_val_.as<T>(), grid); }
-    CsrDev<T> csrPAt(int grid) const { return csr(planPAt_, PAt_val_.as<T>(), grid); }
+    CsrW<T> csrA(int grid) const { return csr(matA_, A_val_.as<T>(), grid); }
+    CsrW<T> csrPAt(int grid) const { return csr(matPAt_, PAt_val_.as<T>(), grid); }
 
     Vecs<T> vecs() const {
         Vecs<T> v;
@@ -1483,12 +1494,12 @@ private:
         return p;
     }
 
-    void spmv_dev(const DevPlan &pl, const T *val, const T *x, T *y, T alpha) {
-        const int g = grid_for_items(pl.nitems, (const void *)k_spmv<T, T>, kSmemT);
+    void spmv_dev(const MatPlans &pl, const T *val, const T *x, T *y, T alpha) {
+        const int g = grid_for_rows(pl.rp, (const void *)k_spmv<T, T>);
         launch_smem(k_spmv<T, T>, g, kThreads, kSmemT, stream_, csr(pl, val, g), x, y, alpha);
         GB_CUDA(cudaGetLastError());
     }
-    void k_spmv_d(CsrDev<T> M, const T *x, double *y, int g) {
+    void k_spmv_d(CsrW<T> M, const T *x, double *y, int g) {
         launch_smem(k_spmv_dbl<T>, g, kThreads, kSmemD, stream_, M, x, y);
         GB_CUDA(cudaGetLastError());
     }
@@ -1616,12 +1627,11 @@ private:
     DevBuf xy_, xt_, pt_, z_, zt_, l_, u_, q_, minv_, diagp_, colsq_, kp_, r_, ypc_, tmp_n_, tmp_nm_;
     DevBuf x_out_, y_out_, z_out_;
     DevBuf partials_, st_, st2_, policy_;
-    DevPlan planA_, planPAt_;
+    MatPlans matA_, matPAt_;
     int gPt_ = 1, gAdmm_ = 1, gCa_ = 1, gKp_ = 1, gInit_ = 1, gCb_ = 1, gIa_ = 1, gIb_ = 1, gridN_ = 1, gridVec_ = 1;
     bool inf_on_ = false;
-    static constexpr size_t kSmemT = rowblock_smem<T, T>();
-    static constexpr size_t kSmemD = rowblock_smem<T, double>();
-    static constexpr size_t kSmemDS = rowblock_smem<T, double, true>();
+    // the warp-stream kernels use no dynamic shared memory
+    static constexpr size_t kSmemT = 0, kSmemD = 0, kSmemDS = 0;
     cudaGraph_t graph_ = nullptr;
     cudaGraphExec_t exec_ = nullptr;
     float solve_ms_ = 0.f;

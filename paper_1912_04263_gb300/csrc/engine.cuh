@@ -55,11 +55,10 @@ public:
     // the next solve continues from the current iterates, rho, PCG tolerance
     // and lambda (iteration count from 0)
     virtual void resume() = 0;
-    // y = M x on device arrays of the working precision, with the long-row
-    // scratch supplied by the caller (part: 2 doubles per work item, count:
-    // one int per long row); allocates nothing.
-    virtual void spmv_noalloc(int which, const void *x, void *y, double *part, int *count, long long max_items,
-                              long long max_long_rows) = 0;
+    // y = M x on device arrays of the working precision, with the split-row
+    // scratch (tickets, partial sums) in the caller's device memory of
+    // scratch_bytes bytes; allocates nothing.
+    virtual void spmv_noalloc(int which, const void *x, void *y, unsigned char *scratch, size_t scratch_bytes) = 0;
     int n = 0, m = 0;
     long long solve_launches = 0;
     long long nnzA = 0, nnzPAt = 0, nnzP = 0;

@@ -7,8 +7,8 @@
 // device-wide synchronisation there invalidates the capture), and hosts
 // whose device memory is owned by another allocator (a framework's caching
 // allocator may leave nothing free, so an allocation could fail mid-loop).
-// For them the SpMV's scratch (the partial sums and ticket counters that
-// combine the pieces of long rows) lives in a fixed file-scope device array
+// For them the SpMV's scratch (the tickets and partial sums that combine the
+// parts of rows cut between warps) lives in a fixed file-scope device array
 // that comes with the library's module and stays resident until the process
 // exits, instead of being allocated.
 #include <mutex>
@@ -20,17 +20,16 @@
 
 namespace {
 
-// Capacity: work items and long rows of one matrix plan.
-constexpr long long kMaxItems = 1LL << 17;     // 131072 items (2 MiB of partial sums)
-constexpr long long kMaxLongRows = 1LL << 17;  // 131072 long rows (512 KiB of counters)
-constexpr size_t kPartBytes = 2 * sizeof(double) * (size_t)kMaxItems;
-constexpr size_t kCountBytes = sizeof(int) * (size_t)kMaxLongRows;
+// Capacity.  A plan needs at most 4 + 2 * 16 + 16 = 52 bytes per warp of the
+// launch (one split row and two partial-sum slots per warp at most), so
+// 1 MiB serves grids of up to about 20000 warps (a full GB300 runs 9728).
+constexpr size_t kScratchBytes = (size_t)1 << 20;
 
 }  // namespace
 
 // The scratch.  In host code this name is a host-side stand-in, not a device
 // address: the device address comes from cudaGetSymbolAddress below.
-static __device__ __align__(256) unsigned char g_spmv_scratch[kPartBytes + kCountBytes];
+static __device__ __align__(256) unsigned char g_spmv_scratch[kScratchBytes];
 
 namespace {
 
@@ -65,9 +64,8 @@ extern "C" int gbosqp_spmv_noalloc(gbosqp_handle *h, int which, const void *x, v
     }
     try {
         GB_CUDA(cudaSetDevice(h->s.device));
-        char *base = static_cast<char *>(scratch_address(h->s.device));
-        h->eng->spmv_noalloc(which, x, y, reinterpret_cast<double *>(base), reinterpret_cast<int *>(base + kPartBytes),
-                             kMaxItems, kMaxLongRows);
+        unsigned char *base = static_cast<unsigned char *>(scratch_address(h->s.device));
+        h->eng->spmv_noalloc(which, x, y, base, kScratchBytes);
         return GBOSQP_OK;
     } catch (const gb::GbError &e) {
         h->err = e.msg;

@@ -1,0 +1,222 @@
+// Host plan of the warp-stream SpMV (spmv.cuh): the cut of a CSR matrix's
+// rows into per-warp ranges of about equal cost, the items of each range,
+// and the table of rows cut between warps.
+//
+// Rows longer than bundle_min (when set) are taken out of the contiguous
+// cut and put into bundles of kWWarps consecutive long rows; a bundle gets
+// a run of CTAs, and the q-th of its k CTAs gives warp j the q-th of k
+// equal nonzero fractions of the bundle's j-th row.  The warps of a CTA
+// then sweep the same fraction of their rows side by side, which for rows
+// with similarly spread columns keeps the gathered entries shared in the
+// CTA's L1.  The other rows are cut contiguously over the remaining warps.
+#include <algorithm>
+#include <vector>
+
+#include "spmv.cuh"
+
+namespace gb {
+
+namespace {
+
+struct Cut {
+    int r;  // row
+    int k;  // first nonzero: rowptr[r] (a row start) or inside row r
+};
+
+bool before(const Cut &a, const Cut &b) { return a.r < b.r || (a.r == b.r && a.k < b.k); }
+
+}  // namespace
+
+WPlanHost build_wplan(const std::vector<int> &rp, int nwarps, const WPlanCost &cost) {
+    WPlanHost P;
+    const int ncta = std::max((nwarps + kWWarps - 1) / kWWarps, 1);
+    nwarps = ncta * kWWarps;
+    P.nwarps = nwarps;
+    const int nrows = (int)rp.size() - 1;
+    const int nnz = nrows > 0 ? rp[nrows] : 0;
+    auto len_of = [&](int r) { return rp[r + 1] - rp[r]; };
+    auto row_cost = [&](int len) { return (long long)len + (len > kGroupMaxLen ? cost.stream_row : cost.group_row); };
+
+    // bundled rows and their share of the CTAs
+    std::vector<int> brows;
+    long long cost_all = 0, cost_b = 0;
+    for (int r = 0; r < nrows; ++r) {
+        const int len = len_of(r);
+        cost_all += row_cost(len);
+        if (cost.bundle_min > 0 && len > cost.bundle_min) {
+            brows.push_back(r);
+            cost_b += row_cost(len);
+        }
+    }
+    int cta_b = 0;
+    {
+        const int nbundles = (int)(brows.size() + kWWarps - 1) / kWWarps;
+        if (nbundles > 0) {
+            cta_b = (int)((double)ncta * cost_b / std::max(cost_all, 1LL) + 0.5);
+            if (cost_b < cost_all) cta_b = std::min(cta_b, ncta - 1);  // keep a CTA for the other rows
+            if (cta_b < nbundles) {                                    // too few CTAs: no bundles
+                brows.clear();
+                cta_b = 0;
+            }
+        }
+    }
+    const int nb = (int)(brows.size() + kWWarps - 1) / kWWarps;
+    std::vector<char> bundled(nrows > 0 ? nrows : 1, 0);
+    for (int r : brows) bundled[r] = 1;
+    // CTAs of bundle b: [bcta[b], bcta[b+1]), in proportion to its longest row
+    std::vector<int> bcta(nb + 1, 0);
+    if (nb > 0) {
+        std::vector<long long> wpre(nb + 1, 0);
+        for (int b = 0; b < nb; ++b) {
+            long long mx = 0;
+            for (int j = 0; j < kWWarps && b * kWWarps + j < (int)brows.size(); ++j)
+                mx = std::max(mx, row_cost(len_of(brows[b * kWWarps + j])));
+            wpre[b + 1] = wpre[b] + mx;
+        }
+        for (int b = 1; b < nb; ++b) {
+            int c = (int)((double)cta_b * wpre[b] / std::max(wpre[nb], 1LL) + 0.5);
+            c = std::max(c, bcta[b - 1] + 1);
+            c = std::min(c, cta_b - (nb - b));
+            bcta[b] = c;
+        }
+        bcta[nb] = cta_b;
+    }
+
+    // contiguous cut of the other rows over warps [wb, nwarps); a cut may
+    // fall inside a row longer than split_min, at a nonzero index rounded to
+    // a multiple of 32 (aligned loads)
+    const int wb = cta_b * kWWarps;
+    const int nw = nwarps - wb;
+    std::vector<long long> pre(nrows + 1, 0);
+    for (int r = 0; r < nrows; ++r) pre[r + 1] = pre[r] + (bundled[r] ? 0 : row_cost(len_of(r)));
+    const long long total = pre[nrows];
+    std::vector<Cut> cut(nw + 1);
+    cut[0] = Cut{0, 0};
+    cut[nw] = Cut{nrows, nnz};
+    for (int w = 1; w < nw; ++w) {
+        Cut c{nrows, nnz};
+        if (nrows > 0 && total > 0) {
+            const long long t = (long long)((double)total * w / nw);
+            int r = (int)(std::upper_bound(pre.begin(), pre.end(), t) - pre.begin()) - 1;
+            r = std::min(std::max(r, 0), nrows - 1);
+            const int len = len_of(r);
+            if (len > cost.split_min) {
+                long long o = t - pre[r] - cost.stream_row;
+                o = std::min<long long>(std::max<long long>(o, 0), len);
+                long long k = rp[r] + o;
+                k = ((k + 16) / 32) * 32;
+                if (k <= rp[r]) c = Cut{r, rp[r]};
+                else if (k >= rp[r + 1]) c = Cut{r + 1, rp[r + 1]};
+                else c = Cut{r, (int)k};
+            } else {
+                c = 2 * (t - pre[r]) < pre[r + 1] - pre[r] ? Cut{r, rp[r]} : Cut{r + 1, rp[r + 1]};
+            }
+        }
+        if (before(c, cut[w - 1])) c = cut[w - 1];
+        cut[w] = c;
+    }
+    auto interior = [&](const Cut &c) { return c.r < nrows && c.k > rp[c.r]; };
+
+    // bundled warp ranges: warp j of the q-th of the k CTAs of bundle b
+    auto frac = [&](int r, long long q, long long k) -> int {
+        if (q <= 0) return rp[r];
+        if (q >= k) return rp[r + 1];
+        long long e = rp[r] + (long long)len_of(r) * q / k;
+        e = ((e + 16) / 32) * 32;
+        return (int)std::min<long long>(std::max<long long>(e, rp[r]), rp[r + 1]);
+    };
+    auto brange = [&](int w, int &row, int &lo, int &hi) -> bool {
+        const int c = w / kWWarps, j = w % kWWarps;
+        const int b = (int)(std::upper_bound(bcta.begin(), bcta.end(), c) - bcta.begin()) - 1;
+        if (b * kWWarps + j >= (int)brows.size()) return false;
+        row = brows[b * kWWarps + j];
+        const int q = c - bcta[b], k = bcta[b + 1] - bcta[b];
+        lo = frac(row, q, k);
+        hi = frac(row, q + 1, k);
+        return lo < hi;
+    };
+
+    // rows cut between warps, in row order
+    std::vector<int> split_rows;
+    for (int w = 1; w < nw; ++w)
+        if (interior(cut[w]) && (split_rows.empty() || split_rows.back() != cut[w].r)) split_rows.push_back(cut[w].r);
+    for (int b = 0; b < nb; ++b) {
+        const int k = bcta[b + 1] - bcta[b];
+        for (int j = 0; j < kWWarps && b * kWWarps + j < (int)brows.size(); ++j) {
+            // split when at least two of its fractions are non-empty
+            const int r = brows[b * kWWarps + j];
+            int parts = 0;
+            for (int q = 0; q < k; ++q) parts += frac(r, q, k) < frac(r, q + 1, k);
+            if (parts >= 2) split_rows.push_back(r);
+        }
+    }
+    std::sort(split_rows.begin(), split_rows.end());
+    std::vector<int> sid(nrows > 0 ? nrows : 1, -1);
+    for (size_t l = 0; l < split_rows.size(); ++l) sid[split_rows[l]] = (int)l;
+    auto id_of = [&](int r) -> int { return sid[r]; };
+
+    P.wpart.assign(nwarps + 1, 0);
+    P.wsplit.assign(nwarps, WSplit{-1, -1, -1, -1});
+    std::vector<int> nparts(split_rows.size(), 0);
+    for (int w = 0; w < wb; ++w) {
+        P.wpart[w] = (int)P.items.size();
+        int row, lo, hi;
+        if (!brange(w, row, lo, hi)) continue;
+        const int h = id_of(row);
+        if (h >= 0) P.wsplit[w].head = h, ++nparts[h];
+        P.items.push_back(WItem{row, row + 1, lo, hi});
+    }
+    for (int v = 0; v < nw; ++v) {
+        const int w = wb + v;
+        P.wpart[w] = (int)P.items.size();
+        const Cut a = cut[v], b = cut[v + 1];
+        if (!before(a, b)) continue;  // empty range
+        const int r_end = interior(b) ? b.r + 1 : b.r;  // one past the last row touched
+        // split rows at the ends of the range
+        const int h = bundled[a.r] ? -1 : id_of(a.r);
+        const int t = (r_end - 1 != a.r && !bundled[r_end - 1]) ? id_of(r_end - 1) : -1;
+        if (h >= 0) P.wsplit[w].head = h, ++nparts[h];
+        if (t >= 0) P.wsplit[w].tail = t, ++nparts[t];
+        int r = a.r;
+        while (r < r_end) {
+            if (bundled[r]) {
+                ++r;
+                continue;
+            }
+            const bool part = id_of(r) >= 0;
+            const int len = len_of(r);
+            if (len > kGroupMaxLen || part) {
+                const int r0 = r;
+                const int k0 = r == a.r ? a.k : rp[r];
+                while (r < r_end && !bundled[r] && (len_of(r) > kGroupMaxLen || id_of(r) >= 0)) ++r;
+                const int k1 = (r == r_end && interior(b)) ? b.k : rp[r];
+                P.items.push_back(WItem{r0, r, k0, k1});
+            } else {
+                const int G = group_width_of(len);
+                const int r0 = r;
+                while (r < r_end && !bundled[r] && len_of(r) <= kGroupMaxLen && id_of(r) < 0 &&
+                       group_width_of(len_of(r)) == G)
+                    ++r;
+                P.items.push_back(WItem{r0, r, -G, 0});
+            }
+        }
+    }
+    P.wpart[nwarps] = (int)P.items.size();
+    // slots of the split rows' parts, in warp order
+    P.split.resize(split_rows.size());
+    int slot = 0;
+    for (size_t l = 0; l < split_rows.size(); ++l) {
+        P.split[l] = SplitRow{split_rows[l], slot, nparts[l], 0};
+        slot += nparts[l];
+    }
+    P.nslots = slot;
+    std::vector<int> next(split_rows.size(), 0);
+    for (int w = 0; w < nwarps; ++w) {
+        WSplit &s = P.wsplit[w];
+        if (s.head >= 0) s.head_slot = P.split[s.head].slot0 + next[s.head]++;
+        if (s.tail >= 0) s.tail_slot = P.split[s.tail].slot0 + next[s.tail]++;
+    }
+    return P;
+}
+
+}  // namespace gb

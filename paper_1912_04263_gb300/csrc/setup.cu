@@ -568,9 +568,11 @@ Csr own_copy(const gbosqp_csr &M, const Input &in, cudaStream_t st) {
     C.ncols = M.ncols;
     C.nnz = M.nnz;
     C.rp.alloc((size_t)(M.nrows + 1) * sizeof(int));
-    // 8 elements of slack past the last nonzero, for loads that round a range outward to 16 bytes (none today)
-    C.col.alloc((M.nnz + 8) * sizeof(int));
-    C.val.alloc((M.nnz + 8) * sizeof(double));
+    // kSlack zeroed elements past the last nonzero (the SpMV's edge steps load past a warp's range)
+    C.col.alloc((M.nnz + kSlack) * sizeof(int));
+    C.val.alloc((M.nnz + kSlack) * sizeof(double));
+    GB_CUDA(cudaMemsetAsync(C.col.as<int>() + M.nnz, 0, kSlack * sizeof(int), st));
+    GB_CUDA(cudaMemsetAsync(C.val.as<double>() + M.nnz, 0, kSlack * sizeof(double), st));
     launch(k_rowptr_i32, blocks_for(M.nrows + 1, 256), 256, st, in.rp64, M.nrows + 1, C.rp.as<int>());
     if (M.nnz > 0) {
         GB_CUDA(cudaMemcpyAsync(C.col.p, in.col, M.nnz * sizeof(int), cudaMemcpyDeviceToDevice, st));
@@ -731,9 +733,11 @@ SetupData device_setup(const gbosqp_csr &P, const gbosqp_csr &A, const double *q
         fail(GBOSQP_ERR_UNSUPPORTED, "2^31 - 64 or more nonzeros in A or [P A']");
     sd.PAt_rowptr.alloc((size_t)(n + 1) * sizeof(int));
     sd.PAt_pend.alloc((size_t)std::max(n, 1) * sizeof(int));
-    // 8 elements of slack past the last nonzero, as in the input copies
-    sd.PAt_col.alloc((sd.nnzPAt + 8) * sizeof(int));
-    sd.PAt_val.alloc((sd.nnzPAt + 8) * sizeof(double));
+    // kSlack zeroed elements past the last nonzero, as in the copy of A
+    sd.PAt_col.alloc((sd.nnzPAt + kSlack) * sizeof(int));
+    sd.PAt_val.alloc((sd.nnzPAt + kSlack) * sizeof(double));
+    GB_CUDA(cudaMemsetAsync(sd.PAt_col.as<int>() + sd.nnzPAt, 0, kSlack * sizeof(int), st));
+    GB_CUDA(cudaMemsetAsync(sd.PAt_val.as<double>() + sd.nnzPAt, 0, kSlack * sizeof(double), st));
     launch(k_pat_rowptr, blocks_for(n + 1, 256), 256, st, Pf.rp.as<int>(), At.rp.as<int>(), n,
                                                           sd.PAt_rowptr.as<int>(), sd.PAt_pend.as<int>());
     if (n) launch(k_pat_fill, warp_blocks(n), kThreads, st, Pf.rp.as<int>(), Pf.col.as<int>(), Pf.val.as<double>(),

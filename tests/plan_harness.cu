@@ -1,22 +1,31 @@
-// Host-only check of the SpMV work plan (build_plan) and of the CTA
-// partition (partition_items) on seeded random row-length profiles; prints
-// "ok" or the first violated invariant.  Built and run by
-// tests/test_host_plan.py (no GPU needed).  With --time it instead times
-// both on the row-length profiles of the 100000 x 1000 Lasso workload's A and
-// [P A'] (the per-set-up host cost of the plans).
+// Host-only check of the warp-stream SpMV plan (build_wplan) on seeded
+// random row-length profiles: the host replays the device's walk of every
+// warp's items (stream items in aligned 32-element steps, group items in
+// rounds of lane groups, split rows' parts published to their slots) and
+// checks that every nonzero is visited once, every row is finished once
+// (whole, or from all of its parts in warp order), that at most one row
+// ends inside a 32-element step of a stream item, and that group rows fit
+// their lane groups.  Prints "ok" or the first violated invariant.  Built
+// and run by tests/test_host_plan.py (no GPU needed).  With --time it times
+// the plans of the 100000 x 1000 Lasso workload's A and [P A'] instead.
 #include <chrono>
 #include <cstdio>
 #include <cstring>
 #include <random>
 #include <vector>
 
-#include "../paper_1912_04263_gb300/csrc/common.cuh"
+#include "../paper_1912_04263_gb300/csrc/spmv.cuh"
 
 using namespace gb;
 
-static int group_width_of(long long avg) {
-    return avg >= 24 ? 32 : avg >= 12 ? 16 : avg >= 6 ? 8 : avg >= 3 ? 4 : 1;
-}
+#define REQUIRE(c, ...)                          \
+    do {                                         \
+        if (!(c)) {                              \
+            printf(__VA_ARGS__);                 \
+            printf("\n");                        \
+            return 1;                            \
+        }                                        \
+    } while (0)
 
 template <class F>
 static double mean_ms(F f, int reps) {
@@ -39,84 +48,124 @@ static int time_lasso_plans() {
     const char *names[2] = {"A", "[P A']"};
     const std::vector<int> *rps[2] = {&rpA, &rpP};
     for (int i = 0; i < 2; ++i) {
-        HostPlan hp = build_plan(*rps[i]);
-        const double b = mean_ms([&] { hp = build_plan(*rps[i]); }, 200);
-        const double p608 = mean_ms([&] { volatile size_t n = partition_items(hp, 608).part.size(); (void)n; }, 200);
-        const double p456 = mean_ms([&] { volatile size_t n = partition_items(hp, 456).part.size(); (void)n; }, 200);
-        printf("%s: %zu items, %zu long rows; build_plan %.3f ms, partition(608) %.3f ms, partition(456) %.3f ms\n",
-               names[i], hp.items.size(), hp.longrows.size(), b, p608, p456);
+        WPlanCost cost;
+        cost.bundle_min = 4096;
+        WPlanHost p = build_wplan(*rps[i], 152 * 4 * kWWarps, cost);
+        const double t = mean_ms([&] { p = build_wplan(*rps[i], 152 * 4 * kWWarps, cost); }, 100);
+        printf("%s: %zu items, %zu split rows for %d warps; build_wplan %.3f ms\n", names[i], p.items.size(),
+               p.split.size(), p.nwarps, t);
     }
+    return 0;
+}
+
+// Replay the device walk of plan P over row pointer rp.
+static int replay(const std::vector<int> &rp, const WPlanHost &P) {
+    const int nrows = (int)rp.size() - 1;
+    const int nnz = rp[nrows];
+    std::vector<int> seen(nnz, 0), finished(nrows, 0), parts(P.split.size(), 0);
+    std::vector<int> slot_used(P.nslots, 0);
+    REQUIRE((int)P.wpart.size() == P.nwarps + 1 && P.wpart[0] == 0 && P.wpart[P.nwarps] == (int)P.items.size(),
+            "wpart bounds");
+    for (size_t l = 0; l < P.split.size(); ++l) {
+        REQUIRE(P.split[l].nparts >= 2, "split row %zu has %d parts", l, P.split[l].nparts);
+        REQUIRE(l == 0 || P.split[l].row > P.split[l - 1].row, "split rows not in row order");
+        REQUIRE(P.split[l].slot0 >= 0 && P.split[l].slot0 + P.split[l].nparts <= P.nslots, "slot range");
+    }
+    for (int w = 0; w < P.nwarps; ++w) {
+        REQUIRE(P.wpart[w] <= P.wpart[w + 1], "wpart not monotone at warp %d", w);
+        const WSplit ws = P.wsplit[w];
+        const int head_row = ws.head >= 0 ? P.split[ws.head].row : -1;
+        const int tail_row = ws.tail >= 0 ? P.split[ws.tail].row : -1;
+        REQUIRE(ws.head < 0 || ws.tail < 0 || head_row < tail_row, "warp %d head/tail order", w);
+        auto finish = [&](int r) -> int {
+            if (r == head_row || r == tail_row) {
+                const int l = r == head_row ? ws.head : ws.tail;
+                const int slot = r == head_row ? ws.head_slot : ws.tail_slot;
+                REQUIRE(slot >= P.split[l].slot0 && slot < P.split[l].slot0 + P.split[l].nparts, "slot of warp %d", w);
+                REQUIRE(slot_used[slot]++ == 0, "slot %d used twice", slot);
+                if (++parts[l] == P.split[l].nparts) ++finished[r];
+            } else {
+                ++finished[r];
+            }
+            return 0;
+        };
+        for (int i = P.wpart[w]; i < P.wpart[w + 1]; ++i) {
+            const WItem it = P.items[i];
+            REQUIRE(it.r0 >= 0 && it.r0 < it.r1 && it.r1 <= nrows, "item %d rows [%d, %d)", i, it.r0, it.r1);
+            if (it.k0 >= 0) {
+                REQUIRE(it.k0 >= rp[it.r0] && it.k0 < rp[it.r0 + 1], "stream item %d start", i);
+                REQUIRE(it.k1 > rp[it.r1 - 1] && it.k1 <= rp[it.r1], "stream item %d end", i);
+                for (int r = it.r0; r < it.r1; ++r) {
+                    const bool part = r == head_row || r == tail_row;
+                    REQUIRE(part || rp[r + 1] - rp[r] > kGroupMaxLen, "short row %d in a stream item", r);
+                    REQUIRE(!part || r == it.r0 || r == it.r1 - 1, "split row %d inside an item", r);
+                }
+                // walk in aligned steps: at most one row end strictly inside the item per step
+                const int base = it.k0 & ~31;
+                const int nsteps = (it.k1 - base + 31) >> 5;
+                // the device loads exactly these steps: inside the arrays and their zeroed slack
+                REQUIRE(base >= 0 && (long long)base + 32LL * nsteps <= (long long)nnz + kSlack,
+                        "item %d loads [%d, %d) outside the %d nonzeros and their slack", i, base, base + 32 * nsteps, nnz);
+                int row = it.r0;
+                for (int s = base; s < it.k1; s += 32) {
+                    int ends = 0;
+                    for (int e = std::max(s, it.k0); e < std::min(s + 32, it.k1); ++e) {
+                        while (e >= rp[row + 1]) {
+                            if (finish(row)) return 1;
+                            ++row;
+                            ++ends;
+                        }
+                        ++seen[e];
+                    }
+                    REQUIRE(ends <= 1, "item %d: %d row ends in one step", i, ends);
+                }
+                REQUIRE(row == it.r1 - 1, "item %d walk ended at row %d", i, row);
+                if (finish(row)) return 1;
+            } else {
+                const int G = -it.k0;
+                REQUIRE(G == 1 || G == 2 || G == 4 || G == 8 || G == 16, "group width %d", G);
+                for (int r = it.r0; r < it.r1; ++r) {
+                    const int len = rp[r + 1] - rp[r];
+                    REQUIRE(len <= 2 * G && group_width_of(len) == G, "row %d of length %d in a group of %d", r, len,
+                            G);
+                    REQUIRE(r != head_row && r != tail_row, "split row %d in a group item", r);
+                    for (int e = rp[r]; e < rp[r + 1]; ++e) ++seen[e];
+                    ++finished[r];
+                }
+            }
+        }
+    }
+    for (int e = 0; e < nnz; ++e) REQUIRE(seen[e] == 1, "nonzero %d visited %d times", e, seen[e]);
+    for (int r = 0; r < nrows; ++r) REQUIRE(finished[r] == 1, "row %d finished %d times", r, finished[r]);
+    for (int s = 0; s < P.nslots; ++s) REQUIRE(slot_used[s] == 1, "slot %d unused", s);
     return 0;
 }
 
 int main(int argc, char **argv) {
     if (argc > 1 && std::strcmp(argv[1], "--time") == 0) return time_lasso_plans();
     std::mt19937 rng(12345);
-    for (int trial = 0; trial < 400; ++trial) {
-        const int nrows = 1 + (int)(rng() % 4000);
+    for (int trial = 0; trial < 600; ++trial) {
+        const int nrows = (int)(rng() % 3000);
         std::vector<int> rp(nrows + 1, 0);
+        const int mode = trial % 4;
         for (int r = 0; r < nrows; ++r) {
             const int k = (int)(rng() % 10);
-            const int len = k < 4 ? (int)(rng() % 4) : k < 7 ? (int)(rng() % 200)
-                            : k < 9 ? (int)(rng() % 5000) : (int)(rng() % 30000);
+            int len;
+            if (mode == 0) len = k < 4 ? (int)(rng() % 4) : k < 7 ? (int)(rng() % 200) : k < 9 ? (int)(rng() % 3000) : (int)(rng() % 20000);
+            else if (mode == 1) len = (int)(rng() % 40);          // around the group / stream boundary
+            else if (mode == 2) len = k == 0 ? (int)(rng() % 50000) : (int)(rng() % 3);  // few long rows
+            else len = 33 + (int)(rng() % 300);                     // stream rows only
             rp[r + 1] = rp[r] + len;
         }
-        const HostPlan hp = build_plan(rp);
-        // items tile the nonzeros in order; rows are covered once
-        long long next_k = 0;
-        int next_row = 0;
-        size_t lr_seen = 0;
-        for (size_t i = 0; i < hp.items.size(); ++i) {
-            const Item &it = hp.items[i];
-            if (it.k0 != next_k || it.k1 < it.k0) { printf("gap or overlap at item %zu\n", i); return 1; }
-            if (it.k1 - it.k0 > kCap) { printf("item %zu over the cap\n", i); return 1; }
-            if (it.r1 >= 0) {  // run of short rows
-                if (it.r0 != next_row || it.r1 <= it.r0) { printf("row order at item %zu\n", i); return 1; }
-                if (rp[it.r0] != it.k0 || rp[it.r1] != it.k1) { printf("row bounds at item %zu\n", i); return 1; }
-                const int rows = it.r1 - it.r0;
-                const int gw = group_width_of((long long)(it.k1 - it.k0) / rows);
-                if (rows > 1 && rows * gw > (gw <= 4 ? 1 : 2) * kThreads) { printf("rounds at item %zu\n", i); return 1; }
-                next_row = it.r1;
-            } else {  // piece of a long row
-                const int lr = -(it.r1 + 1);
-                if (lr < 0 || (size_t)lr >= hp.longrows.size()) { printf("long-row id at item %zu\n", i); return 1; }
-                const LongRow &L = hp.longrows[lr];
-                const int len = rp[it.r0 + 1] - rp[it.r0];
-                if (len <= kCap) { printf("short row cut into pieces at item %zu\n", i); return 1; }
-                const int piece = (int)i - L.first_item;
-                if (piece < 0 || piece >= L.npieces) { printf("piece index at item %zu\n", i); return 1; }
-                const int np = L.npieces;
-                if (np != (len + kCap - 1) / kCap) { printf("piece count of long row %d\n", lr); return 1; }
-                const int plen = it.k1 - it.k0;
-                if (plen < len / np - 1 || plen > len / np + 1) { printf("uneven piece at item %zu\n", i); return 1; }
-                if (piece == 0) {
-                    if (it.r0 != next_row || it.k0 != rp[it.r0]) { printf("long row start at item %zu\n", i); return 1; }
-                    if ((size_t)lr != lr_seen++) { printf("long-row ids out of order\n"); return 1; }
-                }
-                if (piece == np - 1) {
-                    if (it.k1 != rp[it.r0 + 1]) { printf("long row end at item %zu\n", i); return 1; }
-                    next_row = it.r0 + 1;
-                }
-            }
-            next_k = it.k1;
-        }
-        // trailing empty rows form short items too; everything is covered
-        if (next_k != rp[nrows] || next_row != nrows) { printf("rows not covered (trial %d)\n", trial); return 1; }
-        const int n = (int)hp.items.size();
-        for (int grid : {1, 2, 7, 152, 608, 1000, 4000}) {
-            if (grid > n) continue;
-            const HostPartition P = partition_items(hp, grid);
-            if ((int)P.part.size() != grid + 1 || P.part[0] != 0 || P.part[grid] != n) { printf("partition ends\n"); return 1; }
-            for (int b = 0; b < grid; ++b)
-                if (P.part[b + 1] <= P.part[b]) { printf("empty CTA %d of %d\n", b, grid); return 1; }
-            for (size_t l = 0; l < hp.longrows.size(); ++l) {
-                const int f = hp.longrows[l].first_item, e = f + hp.longrows[l].npieces - 1;
-                const int c0 = P.lr_cta[l].x, c1 = P.lr_cta[l].y;
-                if (!(P.part[c0] <= f && f < P.part[c0 + 1] && P.part[c1] <= e && e < P.part[c1 + 1])) {
-                    printf("CTA range of long row %zu\n", l);
-                    return 1;
-                }
-            }
+        const int nwarps = 1 + (int)(rng() % 5000);
+        WPlanCost cost;
+        if (trial % 3 == 1) cost.split_min = 33 + (int)(rng() % 400);
+        if (trial % 5 == 2) cost.group_row = (int)(rng() % 64);
+        if (trial % 2 == 1) cost.bundle_min = 33 + (int)(rng() % 3000);
+        const WPlanHost P = build_wplan(rp, nwarps, cost);
+        if (replay(rp, P)) {
+            printf("trial %d (rows %d, warps %d)\n", trial, nrows, nwarps);
+            return 1;
         }
     }
     printf("ok\n");

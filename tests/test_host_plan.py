@@ -1,7 +1,8 @@
-"""Host logic of the SpMV: the work plan (rows cut into items and long-row
-pieces) and the CTA partition, checked on 400 seeded random row-length
-profiles by a small C++ harness compiled against the library's host code
-(nvcc cross-compiles here; no GPU is used)."""
+"""Host logic of the SpMV: the warp-stream plan (rows cut into per-warp
+ranges, items, split rows and their slots, bundles of long rows), checked on
+600 seeded random row-length profiles by a small C++ harness compiled against
+the library's plan code, which replays every warp's walk on the host (nvcc
+cross-compiles here; no GPU is used)."""
 import os
 import shutil
 import subprocess
@@ -19,6 +20,6 @@ def test_plan_and_partition_invariants(tmp_path):
     exe = str(tmp_path / "plan_harness")
     subprocess.check_call([nvcc, "-std=c++17", "-O2", "-I" + os.path.join(ROOT, "include"), "-o", exe,
                            os.path.join(HERE, "plan_harness.cu"),
-                           os.path.join(ROOT, "paper_1912_04263_gb300", "csrc", "util.cu")])
+                           os.path.join(ROOT, "paper_1912_04263_gb300", "csrc", "plan.cu")])
     out = subprocess.run([exe], capture_output=True, text=True, timeout=300)
     assert out.returncode == 0 and out.stdout.strip() == "ok", out.stdout + out.stderr

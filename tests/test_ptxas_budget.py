@@ -1,9 +1,12 @@
 """Register and spill budget of the solve kernels, checked at compile time
 (no GPU): engine.cu is compiled for sm_103a with ptxas's resource report
 into a temporary directory, and every kernel must stay within the register
-count its launch bounds allow and spill nothing, except the two known
-small spills (the FP32 termination check part A, whose compensated sums
-need extra live state, and the test-only SpMV entry point)."""
+count its launch bounds allow and spill no more than the known small
+amounts below.  The warp-stream SpMV kernels of the PCG loop hold their
+next batch of values and columns in registers; what spills is a few words
+of live state, about half of it in the rare path that combines the parts
+of a row cut between warps (its epilogue works on a local reduction
+record), and the checks' compensated FP32 sums need the most."""
 import os
 import re
 import shutil
@@ -16,7 +19,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_1912_04263_gb300", "csrc")
 
 # kernel name fragment -> largest spill (bytes of stores) allowed
-KNOWN_SPILLS = {"k_check_aIfE": 32, "k_spmvIffE": 48}
+KNOWN_SPILLS = {"k_pcg_kpIfE": 8, "k_pcg_initIfE": 48, "k_check_bIfE": 80, "k_inf_bIfE": 8,
+                "k_spmvIffE": 48, "k_spmvIddE": 96, "k_spmv_dblIfE": 48, "k_spmv_dblIdE": 96}
 
 
 def _nvcc():
@@ -67,10 +71,10 @@ def test_no_unexpected_spills(report):
 
 
 def test_register_counts_fit_the_launch_bounds(report):
-    """256 threads per CTA and a 65536-register file: the FP32 SpMV and
-    update kernels are bounded to 4 resident CTAs per SM (64 registers a
-    thread), the FP32 checks and detection kernels to 3 (80), the FP64
-    instantiations to 2 (128); nothing may need more than 128."""
+    """256 threads per CTA and a 65536-register file: the FP32 SpMV
+    kernels of the PCG loop are bounded to 4 resident CTAs per SM (64
+    registers a thread), the FP32 checks and detection kernels to 3 (80), the
+    FP64 instantiations to 2 (128); nothing may need more than 128."""
     for name, r in report.items():
         regs = r.get("regs", 0)
         assert regs <= 128, (name, r)
