@@ -95,7 +95,10 @@ constexpr int kMinBlocks = GB_MIN_BLOCKS;
 // steps of 32 nonzeros per batch of the warp-stream SpMV (see spmv.cuh)
 constexpr int kU = 4;
 // rows longer than this go to CTA bundles in the warp-stream plan
-constexpr int kBundleMin = 4096;
+#ifndef GB_BUNDLE_MIN
+#define GB_BUNDLE_MIN 4096
+#endif
+constexpr int kBundleMin = GB_BUNDLE_MIN;
 
 template <class T>
 __device__ __forceinline__ T clampv(T v, T lo, T hi) {

@@ -240,10 +240,8 @@ __device__ __forceinline__ void stream_item(const CsrW<T> &M, const WItem &it, c
             }
         }
     };
-    auto process = [&](int s0, const T(&v)[U], const int(&c)[U]) {
-        T pr[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) pr[u] = v[u] * gather(c[u]);
+    // add the products of the U steps from s0 to their rows
+    auto sum_batch = [&](int s0, T(&pr)[U]) {
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int s = s0 + u;
@@ -279,6 +277,12 @@ __device__ __forceinline__ void stream_item(const CsrW<T> &M, const WItem &it, c
                 pcur = pnext;
             }
         }
+    };
+    auto process = [&](int s0, const T(&v)[U], const int(&c)[U]) {
+        T pr[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) pr[u] = v[u] * gather(c[u]);
+        sum_batch(s0, pr);
     };
     load(0, va, ca);
     for (int s0 = 0; s0 < nsteps; s0 += 2 * U) {
