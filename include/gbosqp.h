@@ -313,7 +313,10 @@ int gbosqp_admm_iterations(gbosqp_handle *h, int32_t k, int32_t *pcg_per_iter);
  * r_prim, r_dual, eps_prim, eps_dual (unscaled, Section 3.1), the scaled
  * r_prim, r_dual, ||Ax||, ||z||, ||Px||, ||A'y||, ||q|| (used by the rho
  * rule and the PCG tolerance), the objective, the rho the residual-ratio
- * rule would set from this check, and 3 reserved zeros. */
+ * rule would set from this check, and three fields of the solve's state
+ * (not of this evaluation): the PCG tolerance weight lambda, the learned
+ * policy's stall count and its fallback count (decisions the ratio rule
+ * took).  The evaluation itself changes no state of the solve. */
 int gbosqp_check(gbosqp_handle *h, double out[GBOSQP_CHECK_FIELDS]);
 
 /* ---- learned rho policy (not in the paper) ----------------------------- *

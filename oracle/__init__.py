@@ -10,6 +10,9 @@ load or call anything here.
 
 Modules:
   ldl.c / ldl.py  sparse LDL' of the quasi-definite KKT matrix (Section 3.2)
+  schur.c / dense.py  dense Cholesky of the KKT matrix's Schur complement on
+                  the variables (the reduced system of eq. (kkt_red_sc)), for
+                  problems with few variables and many constraints
   admm.py         Ruiz equilibration (Algorithm 2), ADMM (Algorithm 1) with
                   the direct KKT solve, PCG (Algorithm 3) on the reduced KKT
                   system (Section 5.3), residuals and tolerances (Section 3.1),

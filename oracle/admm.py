@@ -71,6 +71,8 @@ class Settings:
     adaptive_rho: bool = True
     rho_vector: bool = False     # eq. (rho_vec): 1e3 rho on equality rows
     refactor_ratio: float = 5.0  # direct solver only: refactor on a 5x change
+    kkt: str = "auto"            # direct solver: "sparse" LDL' of eq. (kkt), "dense" Schur
+                                 # complement (oracle/dense.py), "auto": dense for n >= 2000, m >= 4n
     pcg_lambda: float = 0.15     # Section 5.3.4
     pcg_eps_min: float = 1e-7    # Section 5.3.4
     max_cg_iter: int = 50
@@ -413,6 +415,17 @@ class Result:
     scaled_state: tuple = ()
 
 
+def kkt_factor(P, A, sigma, rv, kind: str = "auto"):
+    """The factor the direct ADMM solves eq. (kkt) with: the sparse LDL' of
+    the whole quasi-definite matrix, or the dense Cholesky of its Schur
+    complement on the variables (many constraints, few variables)."""
+    n, m = P.shape[0], A.shape[0]
+    if kind == "dense" or (kind == "auto" and n >= 2000 and m >= 4 * n):
+        from .dense import DenseSchurFactor
+        return DenseSchurFactor(P, A, sigma, rv)
+    return KKTFactor(P, A, sigma, rv)
+
+
 def _prepare(qp, s: Settings):
     sc = ruiz(qp.P, qp.q, qp.A, qp.l, qp.u, s.scaling_iters)
     return sc
@@ -428,7 +441,7 @@ def solve(qp, settings: Settings | None = None, x0=None, y0=None) -> Result:
     z = sc.A @ x if x0 is not None else np.zeros(m)
     rho = s.rho0
     rv = rho_vector(rho, sc.l, sc.u, s.rho_vector)
-    F = KKTFactor(sc.P, sc.A, s.sigma, rv)
+    F = kkt_factor(sc.P, sc.A, s.sigma, rv, s.kkt)
     status = "max_iter"
     res = None
     hist = [rho]
@@ -460,7 +473,7 @@ def solve(qp, settings: Settings | None = None, x0=None, y0=None) -> Result:
                     max_rel = max(max_rel, F.max_rel_residual)
                     rho = new_rho
                     rv = rho_vector(rho, sc.l, sc.u, s.rho_vector)
-                    F = KKTFactor(sc.P, sc.A, s.sigma, rv)
+                    F = kkt_factor(sc.P, sc.A, s.sigma, rv, s.kkt)
                     hist.append(rho)
     xu, zu, yu = unscale(sc, x, z, y)
     res = residuals(qp.P, qp.q, qp.A, xu, zu, yu, s.eps_abs, s.eps_rel)

@@ -472,7 +472,7 @@ def load_policy(path: str) -> np.ndarray:
 
 
 CHECK_NAMES = ["r_prim", "r_dual", "eps_prim", "eps_dual", "r_prim_s", "r_dual_s", "norm_Ax_s", "norm_z_s",
-               "norm_Px_s", "norm_Aty_s", "norm_q_s", "obj", "rho_ratio"]
+               "norm_Px_s", "norm_Aty_s", "norm_q_s", "obj", "rho_ratio", "lambda", "stall_count", "fallbacks"]
 
 
 def gbosqp_check(h) -> dict:

@@ -1245,7 +1245,8 @@ public:
         Status r = read_status(st2_);
         const double vals[GBOSQP_CHECK_FIELDS] = {r.r_prim, r.r_dual, r.eps_prim, r.eps_dual, r.rp_s, r.rd_s,
                                                   r.ax_s,   r.z_s,    r.px_s,     r.aty_s,    r.qnorm_s, r.obj,
-                                                  rho_ratio(&r), 0.0, 0.0,        0.0};
+                                                  rho_ratio(&r), h.lambda, (double)h.stall_count,
+                                                  (double)h.fallbacks};
         std::memcpy(out, vals, sizeof(vals));
     }
 

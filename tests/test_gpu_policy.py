@@ -4,6 +4,7 @@ oracle.  The network is not in the paper: these pins are finite differences
 import numpy as np
 import pytest
 
+import qpgen
 from oracle import mlp
 
 pytestmark = pytest.mark.gpu
@@ -207,3 +208,81 @@ def test_trained_policy_gain_over_ratio_rule(gb):
     assert its["learned"] <= its["ratio"]
     assert tot["learned"] <= 1.02 * tot["ratio"]
     assert tot["learned"] < tot["fp64"]
+
+
+# ------------------------------------------------ on-device decisions replayed --
+
+def _replay_decisions(gb, qp, flat, decisions):
+    """Run a learned-policy FP32 solve with the host-driven loop, ten
+    iterations (one rho decision) at a time, and replay every decision
+    through the oracle's restatement (oracle.policy.decide) with the check
+    values of the same state.  Returns the compared (device, oracle) pairs."""
+    from oracle import admm, policy
+    st = policy.PolicyState()
+    pairs = []
+    with gb.Solver(qp, precision=gb.FP32, loop_mode=gb.LOOP_HOST, rho_policy=gb.RHO_LEARNED,
+                   policy_params=flat) as s:
+        gb.gbosqp_set_iterates(s.h, np.zeros(qp.n), np.zeros(qp.m), np.zeros(qp.m), np.zeros(qp.n), 0.1)
+        rho, lam = 0.1, 0.15
+        for _ in range(decisions):
+            status, per = gb.gbosqp_admm_iterations(s.h, 10)
+            if status != 0:
+                break
+            c = gb.gbosqp_check(s.h)  # the residuals the decision read (iterates unchanged since)
+            rho_dev = gb.gbosqp_get_iterates(s.h)[4]
+            scaled = admm.Residuals(c["r_prim_s"], c["r_dual_s"], 0.0, 0.0, c["norm_Ax_s"], c["norm_z_s"],
+                                    c["norm_Px_s"], c["norm_Aty_s"], c["norm_q_s"])
+            rho_ref, lam_ref, used = policy.decide(flat, st, scaled, c["r_prim"], c["r_dual"], c["eps_prim"],
+                                                   c["eps_dual"], rho, int(np.sum(per)), 10)
+            lam = lam_ref if lam_ref is not None else lam
+            dev = {"rho": rho_dev, "lambda": c["lambda"], "stalls": int(c["stall_count"]),
+                   "fallbacks": int(c["fallbacks"])}
+            ref = {"rho": rho_ref, "lambda": lam,
+                   "stalls": st.stall_count, "fallbacks": st.fallbacks, "used": used}
+            pairs.append((dev, ref))
+            rho = rho_dev
+    return pairs
+
+
+def test_device_decisions_match_oracle_restatement(gb):
+    """Every rho decision of a learned-policy solve (committed weights) equals
+    the oracle's restatement of readings S11 and S12 on the same check: the
+    new rho to 1e-6 relative (the device forms the features in FP32, the
+    oracle in FP64, before the same BF16 rounding), lambda likewise, and the
+    stall and fallback counters exactly."""
+    import os
+    flat = gb.load_policy(os.path.join(os.path.dirname(gb.__file__), "policy", "rho_policy.bin"))
+    pairs = []
+    for name in ["random_300x3000", "lasso_50x2000", "portfolio_3000x30"]:
+        pairs += _replay_decisions(gb, qpgen.by_name(name, 0), flat, 12)
+    assert len(pairs) >= 8
+    assert any(r["used"] for _, r in pairs), "the network decided nowhere"
+    for dev, ref in pairs:
+        assert abs(dev["rho"] - ref["rho"]) <= 1e-6 * ref["rho"], (dev, ref)
+        assert abs(dev["lambda"] - ref["lambda"]) <= 1e-6 * ref["lambda"], (dev, ref)
+        assert dev["stalls"] == ref["stalls"] and dev["fallbacks"] == ref["fallbacks"], (dev, ref)
+
+
+def test_overflowing_network_is_a_stall(gb):
+    """Finite parameters (1e30) that overflow inside the network give a
+    non-finite output: every decision the network would take counts as a
+    stall and falls back to the ratio rule (reading S12), on the device as in
+    the oracle, with the same stall and fallback counts at every decision."""
+    flat = np.zeros(4622, np.float32)
+    flat[4:8] = 1.0                                  # std
+    off = 8 + 256                                    # W1 = 0
+    flat[off:off + 64] = 1e30                        # b1: every hidden unit of layer 1 is 1e30
+    off += 64
+    flat[off:off + 4096] = 1e30                      # W2: layer 2 sums 64 x 1e60, past the FP32 range
+    off += 4096 + 64
+    flat[off:off + 128] = 1.0                        # W3
+    off += 128 + 2
+    flat[off:off + 4] = [np.log(10.0), 0.05, 0.5, 1.0]
+    assert np.all(np.isfinite(flat))
+    pairs = _replay_decisions(gb, qpgen.by_name("random_300x3000", 0), flat, 8)
+    assert len(pairs) >= 4
+    assert not any(r["used"] for _, r in pairs)
+    for dev, ref in pairs:
+        assert abs(dev["rho"] - ref["rho"]) <= 1e-12 * ref["rho"], (dev, ref)
+        assert dev["stalls"] == ref["stalls"] and dev["fallbacks"] == ref["fallbacks"], (dev, ref)
+    assert pairs[-1][0]["stalls"] >= 1 and pairs[-1][0]["fallbacks"] == len(pairs)

@@ -345,3 +345,46 @@ def test_bf16_gradient_variant_reduces_to_exact_without_rounding(monkeypatch):
     assert abs(l1 - l2) <= 1e-14 * max(1.0, abs(l2))
     for k in g2:
         assert np.allclose(g1[k], g2[k], rtol=1e-12, atol=1e-14)
+
+
+# ------------------------------------------------- dense Schur-complement solve --
+
+def test_schur_matrix_is_p_plus_sigma_plus_atra():
+    """oracle.dense.schur_matrix against the dense product written out."""
+    from oracle import dense
+    rng = np.random.default_rng(11)
+    qp = qpgen.random_qp(40, 300, 2)
+    r = rng.uniform(0.1, 10.0, qp.m)
+    S = dense.schur_matrix(qp.P, qp.A, 1e-3, r)
+    Ad = qp.A.toarray()
+    ref = qp.P.toarray() + 1e-3 * np.eye(qp.n) + Ad.T @ (r[:, None] * Ad)
+    assert np.max(np.abs(S - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+def test_dense_schur_solve_equals_sparse_ldl():
+    """Both factors solve eq. (kkt) for the same right-hand side to 1e-10, on
+    a mid-size random QP after Ruiz scaling, for a scalar rho and a rho
+    vector."""
+    from oracle import dense, ldl
+    qp = qpgen.by_name("random_300x3000", 0)
+    sc = admm.ruiz(qp.P, qp.q, qp.A, qp.l, qp.u, 10)
+    rng = np.random.default_rng(12)
+    rhs = rng.standard_normal(qp.n + qp.m)
+    for rho in (0.1, admm.rho_vector(0.1, sc.l, sc.u, True), 7.0):
+        a = ldl.KKTFactor(sc.P, sc.A, 1e-6, rho).solve(rhs)
+        F = dense.DenseSchurFactor(sc.P, sc.A, 1e-6, rho)
+        b = F.solve(rhs)
+        assert np.max(np.abs(a - b)) <= 1e-10 * np.max(np.abs(a))
+        assert F.max_rel_residual <= 1e-12
+
+
+def test_oracle_solve_same_with_either_factor():
+    """The direct ADMM takes the same path with either factor: the same
+    iteration count and rho history, and iterates equal to 1e-8."""
+    qp = qpgen.by_name("random_300x3000", 0)
+    a = admm.solve(qp, admm.Settings(kkt="sparse"))
+    b = admm.solve(qp, admm.Settings(kkt="dense"))
+    assert a.status == b.status == "solved" and a.iters == b.iters
+    assert np.allclose(a.rho_history, b.rho_history, rtol=1e-12)
+    assert np.max(np.abs(a.x - b.x)) <= 1e-8 * max(1.0, np.max(np.abs(a.x)))
+    assert abs(a.obj - b.obj) <= 1e-9 * max(1.0, abs(a.obj))
