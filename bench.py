@@ -156,6 +156,47 @@ def algorithmic_bytes(kernel: str, n: int, m: int, nnz: int, s: int = 4) -> int:
     raise ValueError(kernel)
 
 
+GOLDEN = os.path.join(ROOT, "tests", "golden", "full_size_optima.json")
+
+# the other measured configurations: (workload, forms, seeds, timed steps)
+EXTRA = [("random_100x1000", ["fp64"], list(range(10)), 3),
+         ("portfolio_100000x1000", ["learned_fp32", "fp64"], [0], 2),
+         ("random_20000x200000", ["learned_fp32", "fp64"], [0], 2)]
+
+
+def golden_optimum(workload: str, seed: int):
+    """f* and the 1-norms of x*, y* of the FP64 oracle's tight solve of the
+    workload, as committed in tests/golden/full_size_optima.json (written by
+    tests/golden/make_full_size_optima.py), or None."""
+    try:
+        with open(GOLDEN) as f:
+            g = json.load(f)[f"{workload}@{seed}"]
+    except (OSError, KeyError, ValueError):
+        return None
+    return g["tight"] if g["tight"]["status"] == "solved" else None
+
+
+def solution_errors(qp, x, y, z, obj, ref) -> dict:
+    """Unscaled residuals of the GPU solution, r_prim = ||A x - z||_inf and
+    r_dual = ||P x + q + A'y||_inf, and its objective 1/2 x'Px + q'x, in FP64
+    on the host from the problem's own data; its objective error against the
+    oracle's optimum ref (f*, ||x*||_1, ||y*||_1): the relative difference
+    |f - f*| / max(|f*|, 1) and the convexity bound max(||y||_1, ||y*||_1)
+    r_prim + r_dual (||x||_1 + ||x*||_1) that |f - f*| must respect."""
+    import numpy as np
+    r_prim = float(np.max(np.abs(qp.A @ x - z), initial=0.0))
+    r_dual = float(np.max(np.abs(qp.P @ x + qp.q + qp.A.T @ y), initial=0.0))
+    f = float(0.5 * x @ (qp.P @ x) + qp.q @ x)
+    out = {"r_prim": r_prim, "r_dual": r_dual, "obj": f, "obj_device": obj}
+    if ref is not None:
+        fs = ref["obj"]
+        out["obj_star"] = fs
+        out["obj_rel_err"] = abs(f - fs) / max(abs(fs), 1.0)
+        out["obj_bound"] = (max(float(np.sum(np.abs(y))), ref["y_norm1"]) * r_prim
+                            + r_dual * (float(np.sum(np.abs(x))) + ref["x_norm1"]))
+    return out
+
+
 def gpu_arm(args) -> None:
     import numpy as np
     import torch
@@ -296,6 +337,11 @@ def gpu_arm(args) -> None:
     for h in handles[1:]:
         gb.osqp_cleanup(h)
 
+    # error of the timed solution against the oracle's optimum (host, FP64)
+    xk, yk, zk = np.empty(n), np.empty(m), np.empty(m)
+    gb.lib().osqp_get_solution(keep, xk.ctypes.data, yk.ctypes.data, zk.ctypes.data)
+    c1_err = solution_errors(qp, xk, yk, zk, gb.osqp_get_info(keep)["obj"], golden_optimum(args.workload, args.seed))
+
     # roofline of the dominant kernels on a live handle (CUDA events)
     reps = 50
     n_, m_, nnz_a, nnz_pat = gb.dims(keep)
@@ -321,6 +367,11 @@ def gpu_arm(args) -> None:
     for h in hs:
         gb.osqp_cleanup(h)
     fp64_step = maxrank(fp64_ms) / max(1, args.steps // 2)
+
+    extra = {}
+    if args.extra and world == 1:
+        for wl, forms, seeds, nsteps in EXTRA:
+            extra[wl] = measure_config(gb, torch, np, stream, dev, local, wl, forms, seeds, nsteps, policy, args)
 
     if rank != 0:
         if dist:
@@ -378,6 +429,8 @@ def gpu_arm(args) -> None:
                 "h2d_bytes_per_step": int(h2d_bytes), "d2h_bytes_per_step": int(d2h_bytes)},
         "clocks": clocks,
         "gpu_launches": launches,
+        "oracle_error": c1_err,
+        "configs": extra,
     }
     if not args.no_cpu_baseline:
         try:
@@ -392,6 +445,79 @@ def gpu_arm(args) -> None:
     print(json.dumps(out))
     if dist:
         dist.destroy_process_group()
+
+
+def measure_config(gb, torch, np, stream, dev, local, workload, forms, seeds, nsteps, policy, args) -> dict:
+    """One more configuration, each form timed like the headline step (set-up
+    from device CSR + solve + solution to device, CUDA events on the library's
+    stream) over nsteps steps after one warm-up, per seed; with the solution's
+    residuals and objective error against the FP64 oracle's tight optimum
+    (committed goldens), and the SpMV kernels' time and GB/s."""
+    import qpgen
+    rec = {"workload": workload_text(workload), "seeds": seeds, "forms": {}}
+    for form in forms:
+        prec = gb.FP64 if form == "fp64" else gb.FP32
+        rows = []
+        for seed in seeds:
+            qp = qpgen.by_name(workload, seed)
+            n, m = qp.n, qp.m
+            P, A = qp.P.tocsr(), qp.A.tocsr()
+            lo = np.where(np.isinf(qp.l), np.sign(qp.l) * 1e20, qp.l)
+            hi = np.where(np.isinf(qp.u), np.sign(qp.u) * 1e20, qp.u)
+            d = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in
+                 {"Prp": P.indptr.astype(np.int64), "Pcol": P.indices.astype(np.int32), "Pval": P.data,
+                  "Arp": A.indptr.astype(np.int64), "Acol": A.indices.astype(np.int32), "Aval": A.data,
+                  "q": qp.q, "l": lo, "u": hi}.items()}
+            xo = torch.empty(n, dtype=torch.float64, device=dev)
+            yo = torch.empty(max(m, 1), dtype=torch.float64, device=dev)
+            zo = torch.empty(max(m, 1), dtype=torch.float64, device=dev)
+
+            def step():
+                s = gb.default_settings(precision=prec, device=local)
+                s.cuda_stream = stream.cuda_stream
+                if form == "learned_fp32" and policy is not None:
+                    s.rho_policy = gb.RHO_LEARNED
+                    s.policy_params = policy.ctypes.data
+                h = gb.osqp_setup_device(d["Prp"], d["Pcol"], d["Pval"], d["Arp"], d["Acol"], d["Aval"],
+                                         d["q"], d["l"], d["u"], n, m, s)
+                st = gb.osqp_solve(h)
+                gb.gbosqp_get_solution_device(h, xo, yo, zo)
+                return h, st
+
+            h, _ = step()
+            gb.osqp_cleanup(h)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            hs = [step() for _ in range(nsteps)]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / nsteps
+            info = gb.osqp_get_info(hs[0][0])
+            row = {"seed": seed, "status": int(hs[0][1]), "time_to_1e3_s": ms / 1000.0,
+                   "solve_ms": info["solve_ms"], "setup_ms": info["setup_ms"], "admm_iters": info["iters"],
+                   "pcg_iters": info["pcg_iters"], "admm_it_per_s": info["iters"] / max(info["solve_ms"] / 1000.0, 1e-12)}
+            if seed == seeds[0]:
+                na, npat = gb.dims(hs[0][0])[2:4]
+                km = {"pcg_kapply": gb.gbosqp_bench_kernel(hs[0][0], gb.K_PCG_KAPPLY, 20),
+                      "pcg_direction": gb.gbosqp_bench_kernel(hs[0][0], gb.K_PCG_DIRECTION, 20)}
+                s_ = 8 if prec == gb.FP64 else 4
+                row["kernel_ms"] = {k: round(v, 5) for k, v in km.items()}
+                row["spmv_gbs"] = {"pcg_kapply": round(algorithmic_bytes("pcg_kapply", n, m, npat, s_) / (km["pcg_kapply"] * 1e-3) / 1e9, 1),
+                                   "pcg_direction": round(algorithmic_bytes("pcg_direction", n, m, na, s_) / (km["pcg_direction"] * 1e-3) / 1e9, 1)}
+            x, y, z = xo.cpu().numpy(), yo[:m].cpu().numpy(), zo[:m].cpu().numpy()
+            row.update(solution_errors(qp, x, y, z, info["obj"], golden_optimum(workload, seed)))
+            row["eps_prim"], row["eps_dual"] = info["eps_prim"], info["eps_dual"]
+            for hh, _ in hs:
+                gb.osqp_cleanup(hh)
+            rows.append(row)
+            del d
+        agg = {k: statistics.median([r[k] for r in rows]) for k in ("time_to_1e3_s", "solve_ms", "admm_iters",
+                                                                      "pcg_iters", "admm_it_per_s")}
+        agg["max_obj_rel_err"] = max((r.get("obj_rel_err", float("nan")) for r in rows), default=None)
+        agg["all_solved"] = all(r["status"] == 1 for r in rows)
+        rec["forms"][form] = {"median": agg, "runs": rows}
+    return rec
 
 
 def reference_arm(args) -> None:
@@ -429,6 +555,10 @@ def main():
     ap.add_argument("--policy", default="learned", choices=["learned", "ratio"],
                     help="rho rule of the FP32 form (learned: the committed trained policy, if present)")
     ap.add_argument("--policy-file", default=None, help="policy weights to use instead of the committed ones")
+    ap.add_argument("--extra", type=int, default=1,
+                    help="1: also time the other configurations (random 100x1000 FP64 over 10 seeds, portfolio "
+                         "100000x1000 and random 20000x200000 learned FP32 vs plain FP64) and report each "
+                         "solution's error against the oracle")
     ap.add_argument("--loop", default="graph", choices=["graph", "host"],
                     help="host: the same kernels driven by a host loop (profilers cannot attribute kernel "
                          "nodes inside graphs with conditional nodes)")

@@ -76,6 +76,7 @@ class Settings:
     pcg_lambda: float = 0.15     # Section 5.3.4
     pcg_eps_min: float = 1e-7    # Section 5.3.4
     max_cg_iter: int = 50
+    pcg_variant: str = "classic"  # solve_pcg: "classic" Algorithm 3 or "single_reduction"
     eps_prim_inf: float = 1e-4   # S17
     eps_dual_inf: float = 1e-4   # S17
 
@@ -388,6 +389,59 @@ def pcg(apply_K, b, x0, Minv, eps, max_iter, relative=False, keep_directions=Fal
     return PCGResult(x, k, norm_inf(r), dirs)
 
 
+def pcg_single_reduction(apply_K, b, x0, Minv, eps, max_iter) -> PCGResult:
+    """Algorithm 3 rearranged so that both inner products of a step come from
+    one reduction (Chronopoulos & Gear, "s-step iterative methods for
+    symmetric linear systems", 1989): besides r and y = M^-1 r the method
+    carries w = K y and s = K p, and per step computes gamma = r'y and
+    delta = w'y of the same vectors.  With beta_i = gamma_i / gamma_(i-1) and
+    alpha_i = gamma_i / (delta_i - beta_i gamma_i / alpha_(i-1)) (alpha_0 =
+    gamma_0 / delta_0, beta_0 = 0) the recurrences
+
+        p_i = -y_i + beta_i p_(i-1),   s_i = -w_i + beta_i s_(i-1),
+        x_(i+1) = x_i + alpha_i p_i,   r_(i+1) = r_i + alpha_i s_i,
+        y_(i+1) = M^-1 r_(i+1),        w_(i+1) = K y_(i+1)
+
+    give the iterates of Algorithm 3 (same sign conventions as pcg(): r = Kx
+    - b, step length of reading S7) in exact arithmetic, at one product with
+    K per step (K y instead of K p; s = K p follows by recurrence).  The
+    stopping test ||r||_inf <= eps of Section 5.3.4 is taken on r_(i+1) as
+    soon as it is formed."""
+    x = np.array(x0, np.float64, copy=True)
+    r = apply_K(x) - b
+    yv = Minv * r
+    k = 0
+    if not norm_inf(r) > eps or max_iter <= 0:
+        return PCGResult(x, 0, norm_inf(r), [])
+    w = apply_K(yv)
+    gamma, delta = float(r @ yv), float(w @ yv)
+    p = np.zeros_like(x)
+    sv = np.zeros_like(x)
+    alpha_prev, gamma_prev = 0.0, 0.0
+    while True:
+        if k == 0:
+            beta = 0.0
+            den = delta
+        else:
+            beta = gamma / gamma_prev if gamma_prev != 0.0 else 0.0
+            den = delta - beta * gamma / alpha_prev
+        if not den > 0.0:
+            break
+        alpha = gamma / den
+        p = -yv + beta * p
+        sv = -w + beta * sv
+        x = x + alpha * p
+        r = r + alpha * sv
+        yv = Minv * r
+        k += 1
+        if not norm_inf(r) > eps or k >= max_iter:
+            break
+        w = apply_K(yv)
+        gamma_prev, alpha_prev = gamma, alpha
+        gamma, delta = float(r @ yv), float(w @ yv)
+    return PCGResult(x, k, norm_inf(r), [])
+
+
 def pcg_tolerance(r_prim_scaled, r_dual_scaled, lam=0.15, eps_min=1e-7) -> float:
     """eps = max(lambda sqrt(||r_prim_bar|| ||r_dual_bar||), eps_min)
     (Section 5.3.4)."""
@@ -505,7 +559,8 @@ def solve_pcg(qp, settings: Settings | None = None, max_iter: int | None = None)
     k = 0
     for k in range(1, limit + 1):
         b = reduced_kkt_rhs(q, A, s.sigma, rv, x, z, y)
-        out = pcg(lambda v: reduced_kkt_apply(P, A, s.sigma, rv, v), b, xt, Minv, eps, s.max_cg_iter)
+        method = pcg_single_reduction if s.pcg_variant == "single_reduction" else pcg
+        out = method(lambda v: reduced_kkt_apply(P, A, s.sigma, rv, v), b, xt, Minv, eps, s.max_cg_iter)
         xt = out.x
         total_cg += out.iters
         per_iter.append(out.iters)

@@ -1,5 +1,6 @@
 """Write tests/golden/full_size_optima.json: the FP64 oracle's optimum of each
-full-size benchmark workload (seed 0), against which the GPU solutions of
+benchmark workload (the full-size Lasso, portfolio and random QPs, seed 0,
+and the 100 x 1000 random QP, seeds 0-9), against which the GPU solutions of
 those workloads are judged (tests/test_gpu_full_size.py, bench.py).
 
 Calls only oracle/ and qpgen/ (the seeded inputs).  For each workload:
@@ -12,7 +13,7 @@ Calls only oracle/ and qpgen/ (the seeded inputs).  For each workload:
 * the oracle's own solve at eps = 1e-3 (the tolerance of the benchmark):
   its objective, residuals and iterations, for the same-eps comparison.
 
-  python tests/golden/make_full_size_optima.py [workload ...]
+  python tests/golden/make_full_size_optima.py [workload@seed ...]
 
 Each workload takes from minutes (Lasso) to about an hour (the 20000 x
 200000 random QP, whose 20000 x 20000 Schur complement is formed and
@@ -35,13 +36,15 @@ import qpgen  # noqa: E402
 from oracle import admm, checks  # noqa: E402
 
 OUT = os.path.join(HERE, "full_size_optima.json")
-WORKLOADS = ["lasso_1000x100000", "random_20000x200000", "portfolio_100000x1000"]
+WORKLOADS = ["random_100x1000@%d" % k for k in range(10)] + ["lasso_1000x100000@0", "portfolio_100000x1000@0",
+                                                             "random_20000x200000@0"]
 TIGHT = 1e-7
 
 
-def one(name: str) -> dict:
-    qp = qpgen.by_name(name, 0)
-    rec = {"workload": name, "seed": 0}
+def one(key: str) -> dict:
+    name, seed = key.split("@")
+    qp = qpgen.by_name(name, int(seed))
+    rec = {"workload": name, "seed": int(seed)}
     for tag, eps in (("eps_1e-3", 1e-3), ("tight", TIGHT)):
         t = time.time()
         r = admm.solve(qp, admm.Settings(eps_abs=eps, eps_rel=eps, max_iter=50000))
@@ -51,7 +54,7 @@ def one(name: str) -> dict:
                     "eps_dual": float(r.res.eps_dual), "x_norm1": float(np.sum(np.abs(r.x))),
                     "y_norm1": float(np.sum(np.abs(r.y))), "rho_history": [float(p) for p in r.rho_history],
                     "kkt_rel_residual": float(r.kkt_rel_residual), "seconds": round(time.time() - t, 1)}
-        print(name, tag, rec[tag], flush=True)
+        print(key, tag, rec[tag], flush=True)
     return rec
 
 
@@ -60,8 +63,8 @@ def main(names):
     if os.path.exists(OUT):
         with open(OUT) as f:
             data = json.load(f)
-    for name in names:
-        data[name] = one(name)
+    for key in names:
+        data[key] = one(key)
         with open(OUT, "w") as f:
             json.dump(data, f, indent=1, sort_keys=True)
 
