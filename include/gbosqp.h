@@ -85,6 +85,17 @@ extern "C" {
 #define GBOSQP_LOOP_HOST 1            /* same kernels driven by a host loop
                                          that reads the stop flags (debug)    */
 
+#define GBOSQP_PCG_CLASSIC 0          /* Algorithm 3: a step is a direction
+                                         kernel (A), a K-apply (P A') and a
+                                         vector update, three grid-wide phases */
+#define GBOSQP_PCG_SINGLE_REDUCTION 1 /* Algorithm 3 rearranged so that a step
+                                         needs one reduction phase (Chronopoulos
+                                         and Gear, 1989): the vector update rides
+                                         on the direction kernel, two kernels a
+                                         step, plus one K-apply of M^-1 r per
+                                         PCG solve; the same iterates in exact
+                                         arithmetic                          */
+
 #define GBOSQP_INFINITY 1e20
 
 /* Matrix selectors for the inspection calls. */
@@ -144,7 +155,8 @@ typedef struct {
                             OSQP's eq. (rho_vec) (fewer ADMM iterations on
                             equality-heavy problems, slower PCG)
                                                              default 0    */
-    int32_t reserved1;
+    int32_t pcg_variant; /* GBOSQP_PCG_CLASSIC | GBOSQP_PCG_SINGLE_REDUCTION
+                                                             default CLASSIC */
     void *cuda_stream;   /* cudaStream_t to run on; NULL: the library
                             creates and owns one.  A caller's stream must
                             stay valid until osqp_cleanup (the handle's
@@ -371,6 +383,10 @@ int gbosqp_resume(gbosqp_handle *h);
 #define GBOSQP_K_CHECK_B 6        /* ||Px + q + A'y|| etc., FP64 (SpMV [P A'])          */
 #define GBOSQP_K_INF_A 7          /* A dx against the bounds, dy clipping (SpMV A)       */
 #define GBOSQP_K_INF_B 8          /* ||P dx||, ||A'dy||, q'dx (SpMV [P A'])              */
+#define GBOSQP_K_PCG_SR_DIRECTION 9 /* single-reduction PCG: p, s = K p, x, r, M^{-1} r
+                                       updates, r'y, ||r||, t = rho A M^{-1} r (SpMV A) */
+#define GBOSQP_K_PCG_SR_KAPPLY 10   /* single-reduction PCG: w = K M^{-1} r, w'y and the
+                                       step coefficients (SpMV [P A'])                */
 
 /* Time `reps` launches of one solve kernel, in the launch configuration the
  * solve uses, on the handle's current vectors, each after a write of twice

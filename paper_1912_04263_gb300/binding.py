@@ -24,6 +24,7 @@ FP32, FP64 = 0, 1
 RHO_RATIO, RHO_LEARNED, RHO_FIXED = 0, 1, 2
 HOST, DEVICE = 0, 1
 LOOP_GRAPH, LOOP_HOST = 0, 1
+PCG_CLASSIC, PCG_SINGLE_REDUCTION = 0, 1
 MAT_A, MAT_PAT = 0, 1
 CHECK_FIELDS = 16
 POLICY_PARAMS = 4622
@@ -44,7 +45,7 @@ class Settings(ctypes.Structure):
                 ("rho_every", ctypes.c_int32), ("scaling_iters", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("rho_policy", ctypes.c_int32), ("P_is_upper", ctypes.c_int32), ("input_location", ctypes.c_int32),
                 ("loop_mode", ctypes.c_int32), ("device", ctypes.c_int32), ("warm_start", ctypes.c_int32),
-                ("rho_vector", ctypes.c_int32), ("reserved1", ctypes.c_int32),
+                ("rho_vector", ctypes.c_int32), ("pcg_variant", ctypes.c_int32),
                 ("cuda_stream", ctypes.c_void_p), ("policy_params", ctypes.c_void_p)]
 
 
@@ -363,7 +364,7 @@ def gbosqp_admm_iterations(h, k: int):
 
 
 (K_PCG_DIRECTION, K_PCG_KAPPLY, K_PCG_UPDATE, K_PCG_INIT, K_ADMM_UPDATE, K_CHECK_A, K_CHECK_B, K_INF_A,
- K_INF_B) = range(9)
+ K_INF_B, K_PCG_SR_DIRECTION, K_PCG_SR_KAPPLY) = range(11)
 
 
 def gbosqp_bench_kernel(h, kernel: int, reps: int) -> float:

@@ -48,6 +48,8 @@ std::string check_settings(const gbosqp_settings &s) {
     if (s.rho_policy < 0 || s.rho_policy > 2) return "unknown rho_policy";
     if (s.warm_start != 0 && s.warm_start != 1) return "warm_start must be 0 or 1";
     if (s.rho_vector != 0 && s.rho_vector != 1) return "rho_vector must be 0 or 1";
+    if (s.pcg_variant != GBOSQP_PCG_CLASSIC && s.pcg_variant != GBOSQP_PCG_SINGLE_REDUCTION)
+        return "pcg_variant must be GBOSQP_PCG_CLASSIC or GBOSQP_PCG_SINGLE_REDUCTION";
     if (s.rho_policy == GBOSQP_RHO_LEARNED && !s.policy_params) return "learned rho policy needs policy_params";
     if (s.input_location != GBOSQP_HOST && s.input_location != GBOSQP_DEVICE) return "bad input_location";
     if (s.loop_mode != GBOSQP_LOOP_GRAPH && s.loop_mode != GBOSQP_LOOP_HOST) return "bad loop_mode";
@@ -95,6 +97,7 @@ int gbosqp_default_settings(gbosqp_settings *s) {
     s->device = 0;
     s->warm_start = 0;
     s->rho_vector = 0;
+    s->pcg_variant = GBOSQP_PCG_CLASSIC;
     s->cuda_stream = nullptr;
     s->policy_params = nullptr;
     return GBOSQP_OK;

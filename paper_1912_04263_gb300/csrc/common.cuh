@@ -108,6 +108,8 @@ struct Status {
     // evolving
     double rho, eps_pcg;
     double ry, pkp, alpha_cg, beta, rnorm;
+    double ry_prev;       // single-reduction PCG: r'y of the previous step
+    int sr_par, sr_pair;  // single-reduction PCG: current state buffer, steps begun in this solve
     int cg_it, breakdown, pcg_continue, admm_continue;
     long long cg_total;
     int k, rho_changed, rho_updates, status;
@@ -133,7 +135,8 @@ struct Status {
     unsigned int tickets[16];
 };
 
-enum Ticket { kTkI1 = 0, kTkK2, kTkK3, kTkC1, kTkC2, kTkSetupA, kTkSetupB, kTkSetupC, kTkMisc, kTkInfA, kTkInfB };
+enum Ticket { kTkI1 = 0, kTkK2, kTkK3, kTkC1, kTkC2, kTkSetupA, kTkSetupB, kTkSetupC, kTkMisc, kTkInfA, kTkInfB,
+              kTkSr1, kTkSr2 };
 
 // ------------------------------------------------------------- reductions
 

@@ -73,12 +73,30 @@ struct Pair<double> {
 template <class T>
 using pair_t = typename Pair<T>::type;
 
+// Single-reduction PCG state of one variable: r, w = K M^-1 r, s = K p and
+// the Jacobi factor M^-1, kept together so that the direction kernel's
+// gather of y = M^-1 r of the next step is one load.
+template <class T>
+struct __align__(4 * sizeof(T)) SrVec {
+    T r, w, s, m;
+};
+
+// Rounded arithmetic with the operation order fixed (no contraction left to
+// the compiler), so that a value formed at a gathered column is bitwise the
+// one formed by the thread that owns that column.
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 template <class T>
 struct Vecs {
     T *xy, *xt, *pt, *dxy;
     T *z, *zt, *l, *u;
     T *q, *minv, *diagp, *colsq, *kp, *r;
     pair_t<T> *ypc;  // (yv = M^{-1} r, pc = previous p) per variable
+    SrVec<T> *sr0, *sr1;  // single-reduction PCG state, two buffers used in turn (nullptr: classic PCG)
+    T *srp;               // single-reduction PCG direction p
     const T *rs;  // R = rho diag(rs), eq. (rho_vec): 1e3 on rows with l = u, else 1;
                   // nullptr for R = rho I (Section 5.3)
     const double *D, *E, *Dinv, *Einv;
@@ -194,6 +212,10 @@ struct EpiInit {
         const T y = v.minv[i] * r;
         v.r[i] = r;
         v.ypc[i] = pair_t<T>{y, T(0)};
+        if (v.sr0) {  // single reduction: w = 0, s = 0, p = 0 before the first step
+            v.sr0[i] = SrVec<T>{r, T(0), T(0), v.minv[i]};
+            v.srp[i] = T(0);
+        }
         red.s[0] += (double)r * (double)y;
         red.m[0] = amax(red.m[0], absd(r));
     }
@@ -213,6 +235,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : 2) k_p
         st->beta = 0.0;
         st->cg_it = 0;
         st->breakdown = 0;
+        if (v.sr0) {  // the first single-reduction pair applies no step (alpha = 0)
+            st->ry_prev = t.s[0];
+            st->alpha_cg = 0.0;
+            st->sr_par = 0;
+            st->sr_pair = 0;
+        }
         const int cont = (!st->device_error && isfinite(t.m[0]) && t.m[0] > st->eps_pcg && st->max_cg > 0) ? 1 : 0;
         st->pcg_continue = cont;
         if (use_h) cudaGraphSetConditional(hP, cont);
@@ -310,6 +338,122 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(Vecs<T> v, Status *st, 
         if (use_h) cudaGraphSetConditional(hP, cont);
     };
     grid_finish<1, 1>(red, partials, &st->tickets[kTkK3], fin);
+}
+
+// ---- single-reduction PCG (Chronopoulos-Gear rearrangement of Algorithm 3)
+//
+// A step i has two kernels.  sr_direction (SpMV A): with alpha_i, beta_i from
+// the previous sr_kapply, every variable forms p_i = -y_i + beta_i p_(i-1),
+// s_i = -w_i + beta_i s_(i-1), x_(i+1) = x_i + alpha_i p_i, r_(i+1) = r_i +
+// alpha_i s_i, y_(i+1) = M^-1 r_(i+1), and the kernel reduces r'y and
+// ||r||_inf of the new r and takes the stopping test; the A SpMV forms
+// t = rho A y_(i+1), forming y_(i+1) at each gathered column from the old
+// state (r, w, s, M^-1 of step i in one SrVec).  The new state goes to the
+// other SrVec buffer, since other CTAs still gather the old one.
+// sr_kapply (SpMV [P A']): w_(i+1) = K y_(i+1) = P y + sigma y + A' t, w'y,
+// and the coefficients alpha_(i+1), beta_(i+1) (Chronopoulos and Gear, 1989).
+// The first pair of a PCG solve runs with alpha = beta = 0 (no step) and
+// yields w_0 = K y_0 and alpha_0 = r'y / w'y; the solve's stopping test is
+// the one of Section 5.3.4 on each new r.
+
+template <class T>
+struct GatherSr {  // y_(i+1) at column c, formed as the owner of c forms it
+    const SrVec<T> *S;
+    T a, b;
+    __device__ __forceinline__ T operator()(int c) const {
+        const SrVec<T> g = S[c];
+        const T sn = fma_rn(b, g.s, -g.w);
+        return mul_rn(g.m, fma_rn(a, sn, g.r));
+    }
+};
+
+template <class T>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : 2)
+    k_sr_direction(CsrW<T> A, Vecs<T> v, Status *st, double *partials, cudaGraphConditionalHandle hP, int use_h) {
+    const T a = T(st->alpha_cg), b = T(st->beta);
+    const int par = st->sr_par;
+    const SrVec<T> *S = par ? v.sr1 : v.sr0;
+    SrVec<T> *Sn = par ? v.sr0 : v.sr1;
+    const int n = v.n;
+    Red<1, 1> red;
+    red.zero();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const SrVec<T> g = S[i];
+        const T sn = fma_rn(b, g.s, -g.w);
+        const T rn = fma_rn(a, sn, g.r);
+        const T yn = mul_rn(g.m, rn);
+        const T p = fma_rn(b, v.srp[i], -mul_rn(g.m, g.r));
+        v.xt[i] = fma_rn(a, p, v.xt[i]);
+        v.srp[i] = p;
+        Sn[i] = SrVec<T>{rn, T(0), sn, g.m};
+        v.pt[i] = yn;
+        red.s[0] += (double)rn * (double)yn;
+        red.m[0] = amax(red.m[0], absd(rn));
+    }
+    EpiDir<T> epi{v.pt + n, v.rs, T(st->rho)};
+    Red<0, 0> none;
+    warp_rows<kU, T, false>(A, GatherSr<T>{S, a, b}, epi, none);
+    auto fin = [&](const Red<1, 1> &t) {
+        if (threadIdx.x != 0) return;
+        st->ry_prev = st->ry;
+        st->ry = t.s[0];
+        st->rnorm = t.m[0];
+        if (st->sr_pair > 0) {  // a step was taken
+            st->cg_it += 1;
+            st->cg_total += 1;
+        }
+        const int cont = (!st->device_error && !st->breakdown && isfinite(t.m[0]) && t.m[0] > st->eps_pcg &&
+                          st->cg_it < st->max_cg) ? 1 : 0;
+        st->pcg_continue = cont;
+        if (use_h) cudaGraphSetConditional(hP, cont);
+    };
+    // the sums come from the vector loop only (not from split rows of A)
+    grid_finish<1, 1>(red, partials, &st->tickets[kTkSr1], fin);
+}
+
+template <class T>
+struct EpiSrW {
+    Vecs<T> v;
+    SrVec<T> *Sn;
+    T sigma;
+    __device__ __forceinline__ void row(int i, T s1, T, Red<1, 0> &red) {
+        const T y = v.pt[i];
+        const T w = s1 + sigma * y;
+        Sn[i].w = w;
+        red.s[0] += (double)w * (double)y;
+    }
+};
+
+template <class T>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : 2)
+    k_sr_kapply(CsrW<T> PAt, Vecs<T> v, Status *st, double *partials) {
+    if (!st->pcg_continue) return;  // the solve stopped at this pair's direction kernel
+    const int par = st->sr_par;
+    EpiSrW<T> epi{v, par ? v.sr0 : v.sr1, T(st->sigma)};
+    Red<1, 0> red;
+    red.zero();
+    warp_rows<kU, T, false>(PAt, GatherVec<T, T>{v.pt}, epi, red);
+    auto fin = [&](const Red<1, 0> &t) {
+        if (threadIdx.x != 0) return;
+        const double delta = t.s[0], gamma = st->ry;
+        double beta = 0.0, den = delta;
+        if (st->sr_pair > 0) {
+            beta = st->ry_prev != 0.0 ? gamma / st->ry_prev : 0.0;
+            den = delta - beta * gamma / st->alpha_cg;
+        }
+        st->pkp = delta;
+        if (den > 0.0 && isfinite(den) && isfinite(beta)) {
+            st->alpha_cg = gamma / den;
+            st->beta = beta;
+        } else {
+            st->alpha_cg = 0.0;
+            st->beta = 0.0;
+            st->breakdown = 1;
+        }
+        st->sr_pair += 1;
+        st->sr_par = par ^ 1;
+    };
+    grid_finish_w<1, 0>(red, PAt, partials, &st->tickets[kTkSr2], fin);
 }
 
 // z~ = A x~;  relaxation, projection, dual update (Algorithm 1 steps 5-7);
@@ -836,6 +980,11 @@ public:
         colsq_ = convert(std::move(sd.colsq), n);
         for (DevBuf *b : {&minv_, &kp_, &r_, &tmp_n_}) b->alloc(sizeof(T) * std::max(n, 1));
         ypc_.alloc(sizeof(pair_t<T>) * std::max(n, 1));
+        sr_ = s.pcg_variant == GBOSQP_PCG_SINGLE_REDUCTION;
+        if (sr_) {
+            for (DevBuf *b : {&sr0_, &sr1_}) b->alloc(sizeof(SrVec<T>) * std::max(n, 1));
+            srp_.alloc(sizeof(T) * std::max(n, 1));
+        }
         tmp_nm_.alloc(sizeof(T) * std::max<size_t>(nm, 1));
         x_out_.alloc(sizeof(double) * std::max(n, 1));
         y_out_.alloc(sizeof(double) * std::max(m, 1));
@@ -862,15 +1011,23 @@ public:
         gCb_ = grid_for_rows(matPAt_.rp, (const void *)k_check_b<T>);
         gIa_ = grid_for_rows(matA_.rp, (const void *)k_inf_a<T>);
         gIb_ = grid_for_rows(matPAt_.rp, (const void *)k_inf_b<T>);
+        if (sr_) {
+            gSr1_ = grid_for_rows(matA_.rp, (const void *)k_sr_direction<T>);
+            gSr2_ = grid_for_rows(matPAt_.rp, (const void *)k_sr_kapply<T>);
+        }
         // vector kernels: about 4 elements per thread
         const int cap = device_sm_count() * 8;
         gridVec_ = std::max(1, std::min(grid_for_n(n, kThreads), cap));
         gridN_ = std::max(1, std::min(grid_for_n(std::max(n, m), kThreads * 4), cap));
-        const int maxgrid = std::max({gPt_, gAdmm_, gCa_, gKp_, gInit_, gCb_, gIa_, gIb_, gridN_, gridVec_});
+        const int maxgrid = std::max({gPt_, gAdmm_, gCa_, gKp_, gInit_, gCb_, gIa_, gIb_, gridN_, gridVec_, gSr1_, gSr2_});
         const int gSpA = grid_for_rows(matA_.rp, (const void *)k_spmv<T, T>);
         const int gSpP = grid_for_rows(matPAt_.rp, (const void *)k_spmv<T, T>);
         for (int g : {gPt_, gAdmm_, gCa_, gIa_, gSpA}) plan_for(matA_, g);
         for (int g : {gKp_, gInit_, gCb_, gIb_, gSpP}) plan_for(matPAt_, g);
+        if (sr_) {
+            plan_for(matA_, gSr1_);
+            plan_for(matPAt_, gSr2_);
+        }
         partials_.alloc(sizeof(double) * (size_t)maxgrid * 8);
         // status block
         Status h;
@@ -955,7 +1112,9 @@ public:
             // pcg_init and admm_update, per PCG step three kernels, per
             // check three kernels (five with infeasibility detection)
             const long long checks = s_.check_every > 0 ? h.k / s_.check_every : 0;
-            solve_launches += 2 + 2LL * h.k + 3LL * h.cg_total + (inf_on_ ? 5LL : 3LL) * checks;
+            // single reduction: a pair of kernels per step plus the first pair of each PCG solve
+            const long long pcg = sr_ ? 2LL * (h.cg_total + h.k) : 3LL * h.cg_total;
+            solve_launches += 2 + 2LL * h.k + pcg + (inf_on_ ? 5LL : 3LL) * checks;
         }
         return h.status;
     }
@@ -1214,12 +1373,9 @@ public:
         int status = 0;
         for (int it = 0; it < k; ++it) {
             launch_init(v, st, 0, 0);
-            int cg = 0;
-            while (read_int(st_, offsetof(Status, pcg_continue))) {
-                launch_step(v, st, 0, 0);
-                ++cg;
-            }
-            if (pcg_per_iter) pcg_per_iter[it] = cg;
+            while (read_int(st_, offsetof(Status, pcg_continue))) launch_step(v, st, 0, 0);
+            // PCG steps taken (the single-reduction PCG runs one more kernel pair than steps)
+            if (pcg_per_iter) pcg_per_iter[it] = read_int(st_, offsetof(Status, cg_it));
             launch_admm(v, st);
             const int kk = read_int(st_, offsetof(Status, k));
             if (kk % s_.check_every == 0) {
@@ -1254,6 +1410,7 @@ public:
         Status h = read_status();
         std::memset(h.tickets, 0, sizeof(h.tickets));
         h.policy = GBOSQP_RHO_FIXED;
+        h.pcg_continue = 1;  // the single-reduction K-apply runs only inside a PCG solve
         GB_CUDA(cudaMemcpyAsync(st2_.p, &h, sizeof(h), cudaMemcpyHostToDevice, stream_));
         Status *st = st2_.as<Status>();
         Vecs<T> v = vecs();
@@ -1276,6 +1433,14 @@ public:
                 case GBOSQP_K_CHECK_B: launch_smem(k_check_b<T>, gCb_, kThreads, kSmemDS, stream_, csrPAt(gCb_), v, st, partials_.as<double>(), policy(), (cudaGraphConditionalHandle)0, 0); break;
                 case GBOSQP_K_INF_A: launch_smem(k_inf_a<T>, gIa_, kThreads, kSmemT, stream_, csrA(gIa_), v, st, partials_.as<double>()); break;
                 case GBOSQP_K_INF_B: launch_smem(k_inf_b<T>, gIb_, kThreads, kSmemT, stream_, csrPAt(gIb_), v, st, partials_.as<double>()); break;
+                case GBOSQP_K_PCG_SR_DIRECTION:
+                    if (!sr_) fail(GBOSQP_ERR_INVALID_ARG, "the handle does not use the single-reduction PCG");
+                    launch(k_sr_direction<T>, gSr1_, kThreads, stream_, csrA(gSr1_), v, st, partials_.as<double>(), (cudaGraphConditionalHandle)0, 0);
+                    break;
+                case GBOSQP_K_PCG_SR_KAPPLY:
+                    if (!sr_) fail(GBOSQP_ERR_INVALID_ARG, "the handle does not use the single-reduction PCG");
+                    launch(k_sr_kapply<T>, gSr2_, kThreads, stream_, csrPAt(gSr2_), v, st, partials_.as<double>());
+                    break;
                 default: fail(GBOSQP_ERR_INVALID_ARG, "unknown kernel selector");
             }
         };
@@ -1478,6 +1643,9 @@ private:
         v.colsq = colsq_.as<T>();
         v.rs = s_.rho_vector ? rs_.as<T>() : nullptr;
         v.ypc = ypc_.as<pair_t<T>>();
+        v.sr0 = sr_ ? sr0_.as<SrVec<T>>() : nullptr;
+        v.sr1 = sr_ ? sr1_.as<SrVec<T>>() : nullptr;
+        v.srp = sr_ ? srp_.as<T>() : nullptr;
         v.kp = kp_.as<T>();
         v.r = r_.as<T>();
         v.D = D_.as<double>();
@@ -1514,6 +1682,12 @@ private:
         GB_CUDA(cudaGetLastError());
     }
     void launch_step(const Vecs<T> &v, Status *st, cudaGraphConditionalHandle h, int use_h) {
+        if (sr_) {
+            launch(k_sr_direction<T>, gSr1_, kThreads, stream_, csrA(gSr1_), v, st, partials_.as<double>(), h, use_h);
+            launch(k_sr_kapply<T>, gSr2_, kThreads, stream_, csrPAt(gSr2_), v, st, partials_.as<double>());
+            GB_CUDA(cudaGetLastError());
+            return;
+        }
         launch_smem(k_pcg_p_t<T>, gPt_, kThreads, kSmemT, stream_, csrA(gPt_), v, st);
         launch_smem(k_pcg_kp<T>, gKp_, kThreads, kSmemT, stream_, csrPAt(gKp_), v, st, partials_.as<double>());
         launch(k_pcg_update<T>, gridVec_, kThreads, stream_, v, st, partials_.as<double>(), h, use_h);
@@ -1578,9 +1752,14 @@ private:
             cudaGraphNode_t ni = add_kernel_smem(body, prev ? &prev : nullptr, k_pcg_init<T>, gInit_, kSmemT, csrPAt(gInit_), v, st, part, hP, 1);
             cudaGraph_t pbody;
             cudaGraphNode_t nw = add_while(body, &ni, hP, &pbody);
-            cudaGraphNode_t a = add_kernel_smem(pbody, nullptr, k_pcg_p_t<T>, gPt_, kSmemT, csrA(gPt_), v, (const Status *)st);
-            cudaGraphNode_t b = add_kernel_smem(pbody, &a, k_pcg_kp<T>, gKp_, kSmemT, csrPAt(gKp_), v, st, part);
-            add_kernel(pbody, &b, k_pcg_update<T>, gridVec_, v, st, part, hP, 1);
+            if (sr_) {
+                cudaGraphNode_t a = add_kernel(pbody, nullptr, k_sr_direction<T>, gSr1_, csrA(gSr1_), v, st, part, hP, 1);
+                add_kernel(pbody, &a, k_sr_kapply<T>, gSr2_, csrPAt(gSr2_), v, st, part);
+            } else {
+                cudaGraphNode_t a = add_kernel_smem(pbody, nullptr, k_pcg_p_t<T>, gPt_, kSmemT, csrA(gPt_), v, (const Status *)st);
+                cudaGraphNode_t b = add_kernel_smem(pbody, &a, k_pcg_kp<T>, gKp_, kSmemT, csrPAt(gKp_), v, st, part);
+                add_kernel(pbody, &b, k_pcg_update<T>, gridVec_, v, st, part, hP, 1);
+            }
             prev = add_kernel_smem(body, &nw, k_admm_update<T>, gAdmm_, kSmemT, csrA(gAdmm_), v, st);
         }
         cudaGraphNode_t ca = add_kernel_smem(body, &prev, k_check_a<T>, gCa_, kSmemD, csrA(gCa_), v, st, part);
@@ -1633,6 +1812,9 @@ private:
     DevBuf partials_, st_, st2_, policy_;
     MatPlans matA_, matPAt_;
     int gPt_ = 1, gAdmm_ = 1, gCa_ = 1, gKp_ = 1, gInit_ = 1, gCb_ = 1, gIa_ = 1, gIb_ = 1, gridN_ = 1, gridVec_ = 1;
+    int gSr1_ = 1, gSr2_ = 1;
+    bool sr_ = false;          // single-reduction PCG
+    DevBuf sr0_, sr1_, srp_;
     bool inf_on_ = false;
     // the warp-stream kernels use no dynamic shared memory
     static constexpr size_t kSmemT = 0, kSmemD = 0, kSmemDS = 0;

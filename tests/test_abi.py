@@ -130,7 +130,9 @@ def test_binding_constants_match_the_header():
              "CHECK_FIELDS": gb.CHECK_FIELDS, "POLICY_PARAMS": gb.POLICY_PARAMS, "INFINITY": gb.INFINITY,
              "K_PCG_DIRECTION": gb.K_PCG_DIRECTION, "K_PCG_KAPPLY": gb.K_PCG_KAPPLY, "K_PCG_UPDATE": gb.K_PCG_UPDATE,
              "K_PCG_INIT": gb.K_PCG_INIT, "K_ADMM_UPDATE": gb.K_ADMM_UPDATE, "K_CHECK_A": gb.K_CHECK_A,
-             "K_CHECK_B": gb.K_CHECK_B, "K_INF_A": gb.K_INF_A, "K_INF_B": gb.K_INF_B}
+             "K_CHECK_B": gb.K_CHECK_B, "K_INF_A": gb.K_INF_A, "K_INF_B": gb.K_INF_B,
+             "K_PCG_SR_DIRECTION": gb.K_PCG_SR_DIRECTION, "K_PCG_SR_KAPPLY": gb.K_PCG_SR_KAPPLY,
+             "PCG_CLASSIC": gb.PCG_CLASSIC, "PCG_SINGLE_REDUCTION": gb.PCG_SINGLE_REDUCTION}
     for name, value in pairs.items():
         assert name in defs, name
         assert defs[name] == value, (name, defs[name], value)
