@@ -43,6 +43,7 @@
 #include <cstddef>
 #include <initializer_list>
 #include <cstring>
+#include <future>
 #include <map>
 #include <memory>
 #include <string>
@@ -762,14 +763,14 @@ struct EpiStore {
 };
 
 template <class T, class Acc>
-__global__ void __launch_bounds__(kThreads) k_spmv(CsrW<T> M, const T *x, T *y, Acc alpha) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : 2) k_spmv(CsrW<T> M, const T *x, T *y, Acc alpha) {
     EpiStore<T, Acc> epi{y, alpha};
     Red<0, 0> red;
     warp_rows<kU, Acc, false>(M, GatherVec<T, Acc>{x}, epi, red);
 }
 
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_spmv_dbl(CsrW<T> M, const T *x, double *y) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_spmv_dbl(CsrW<T> M, const T *x, double *y) {
     EpiStore<double, double> epi{y, 1.0};
     Red<0, 0> red;
     warp_rows<kU, double, false>(M, GatherVec<T, T>{x}, epi, red);
@@ -1022,11 +1023,13 @@ public:
         const int maxgrid = std::max({gPt_, gAdmm_, gCa_, gKp_, gInit_, gCb_, gIa_, gIb_, gridN_, gridVec_, gSr1_, gSr2_});
         const int gSpA = grid_for_rows(matA_.rp, (const void *)k_spmv<T, T>);
         const int gSpP = grid_for_rows(matPAt_.rp, (const void *)k_spmv<T, T>);
-        for (int g : {gPt_, gAdmm_, gCa_, gIa_, gSpA}) plan_for(matA_, g);
-        for (int g : {gKp_, gInit_, gCb_, gIb_, gSpP}) plan_for(matPAt_, g);
-        if (sr_) {
-            plan_for(matA_, gSr1_);
-            plan_for(matPAt_, gSr2_);
+        {
+            std::vector<int> gA{gPt_, gAdmm_, gCa_, gIa_, gSpA}, gP{gKp_, gInit_, gCb_, gIb_, gSpP};
+            if (sr_) {
+                gA.push_back(gSr1_);
+                gP.push_back(gSr2_);
+            }
+            build_plans(gA, gP);
         }
         partials_.alloc(sizeof(double) * (size_t)maxgrid * 8);
         // status block
@@ -1553,12 +1556,34 @@ private:
 
     // The plan of matrix mp for a launch of `grid` CTAs (built once per
     // grid size; kernels with the same grid share it).
-    const WDev &plan_for(const MatPlans &mp, int grid) const {
-        auto it = mp.by_grid.find(grid);
-        if (it != mp.by_grid.end()) return it->second;
+    static WPlanHost host_plan(const MatPlans &mp, int grid) {
         WPlanCost cost;
         cost.bundle_min = kBundleMin;
-        const WPlanHost hp = build_wplan(mp.rp, grid * kWWarps, cost);
+        return build_wplan(mp.rp, grid * kWWarps, cost);
+    }
+
+    // Build the host plans of all the given grids of both matrices on host
+    // threads at once, then upload them (the device calls stay on this thread).
+    void build_plans(const std::vector<int> &gA, const std::vector<int> &gP) {
+        std::vector<std::pair<const MatPlans *, int>> todo;
+        for (int g : gA)
+            if (!matA_.by_grid.count(g) && std::find(todo.begin(), todo.end(), std::make_pair((const MatPlans *)&matA_, g)) == todo.end())
+                todo.emplace_back(&matA_, g);
+        for (int g : gP)
+            if (!matPAt_.by_grid.count(g) && std::find(todo.begin(), todo.end(), std::make_pair((const MatPlans *)&matPAt_, g)) == todo.end())
+                todo.emplace_back(&matPAt_, g);
+        std::vector<std::future<WPlanHost>> fut;
+        for (auto &t : todo) fut.push_back(std::async(std::launch::async, host_plan, std::cref(*t.first), t.second));
+        for (size_t i = 0; i < todo.size(); ++i) {
+            WPlanHost hp = fut[i].get();
+            plan_for(*todo[i].first, todo[i].second, &hp);
+        }
+    }
+
+    const WDev &plan_for(const MatPlans &mp, int grid, const WPlanHost *prebuilt = nullptr) const {
+        auto it = mp.by_grid.find(grid);
+        if (it != mp.by_grid.end()) return it->second;
+        const WPlanHost hp = prebuilt ? *prebuilt : host_plan(mp, grid);
         WDev d;
         d.nwarps = hp.nwarps;
         d.nsplit = (int)hp.split.size();

@@ -37,15 +37,21 @@ WPlanHost build_wplan(const std::vector<int> &rp, int nwarps, const WPlanCost &c
     auto len_of = [&](int r) { return rp[r + 1] - rp[r]; };
     auto row_cost = [&](int len) { return (long long)len + (len > kGroupMaxLen ? cost.stream_row : cost.group_row); };
 
-    // bundled rows and their share of the CTAs
+    // bundled rows and their share of the CTAs; prefix of the costs of the
+    // other rows (one pass)
     std::vector<int> brows;
+    std::vector<long long> pre(nrows + 1, 0);
     long long cost_all = 0, cost_b = 0;
     for (int r = 0; r < nrows; ++r) {
         const int len = len_of(r);
-        cost_all += row_cost(len);
+        const long long c = row_cost(len);
+        cost_all += c;
         if (cost.bundle_min > 0 && len > cost.bundle_min) {
             brows.push_back(r);
-            cost_b += row_cost(len);
+            cost_b += c;
+            pre[r + 1] = pre[r];
+        } else {
+            pre[r + 1] = pre[r] + c;
         }
     }
     int cta_b = 0;
@@ -57,6 +63,7 @@ WPlanHost build_wplan(const std::vector<int> &rp, int nwarps, const WPlanCost &c
             if (cta_b < nbundles) {                                    // too few CTAs: no bundles
                 brows.clear();
                 cta_b = 0;
+                for (int r = 0; r < nrows; ++r) pre[r + 1] = pre[r] + row_cost(len_of(r));
             }
         }
     }
@@ -87,18 +94,17 @@ WPlanHost build_wplan(const std::vector<int> &rp, int nwarps, const WPlanCost &c
     // a multiple of 32 (aligned loads)
     const int wb = cta_b * kWWarps;
     const int nw = nwarps - wb;
-    std::vector<long long> pre(nrows + 1, 0);
-    for (int r = 0; r < nrows; ++r) pre[r + 1] = pre[r] + (bundled[r] ? 0 : row_cost(len_of(r)));
     const long long total = pre[nrows];
     std::vector<Cut> cut(nw + 1);
     cut[0] = Cut{0, 0};
     cut[nw] = Cut{nrows, nnz};
+    int rw = 0;  // the targets grow with w: the row holding target t is found by walking forward
     for (int w = 1; w < nw; ++w) {
         Cut c{nrows, nnz};
         if (nrows > 0 && total > 0) {
             const long long t = (long long)((double)total * w / nw);
-            int r = (int)(std::upper_bound(pre.begin(), pre.end(), t) - pre.begin()) - 1;
-            r = std::min(std::max(r, 0), nrows - 1);
+            while (rw < nrows - 1 && pre[rw + 1] <= t) ++rw;  // the last row r with pre[r] <= t
+            const int r = rw;
             const int len = len_of(r);
             if (len > cost.split_min) {
                 long long o = t - pre[r] - cost.stream_row;
