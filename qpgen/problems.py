@@ -358,6 +358,7 @@ def by_name(name: str, seed: int = 0) -> QP:
         "lasso_1000x100000": lambda s: lasso_qp(1000, 100000, s),
         "portfolio_100000x1000": lambda s: portfolio_qp(100000, 1000, s),
         "random_20000x200000": lambda s: random_qp(20000, 200000, s, p_density=5e-4, a_density=0.01),
+        "random_5000x50000": lambda s: random_qp(5000, 50000, s),  # held-out workload of the learned policy
         # small members of the same families
         "lasso_50x2000": lambda s: lasso_qp(50, 2000, s),
         "lasso_100x5000": lambda s: lasso_qp(100, 5000, s),

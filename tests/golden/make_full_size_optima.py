@@ -11,7 +11,9 @@ Calls only oracle/ and qpgen/ (the seeded inputs).  For each workload:
   is then applied with ||x - x*||_1 <= ||x||_1 + ||x*||_1), its residuals and
   iteration count;
 * the oracle's own solve at eps = 1e-3 (the tolerance of the benchmark):
-  its objective, residuals and iterations, for the same-eps comparison.
+  its objective, residuals and iterations, for the same-eps comparison;
+* x* in FP32 in full_size_xstar.npz (the bound's ||x - x*||_1 then carries
+  at most 2^-24 ||x*||_1 of rounding).
 
   python tests/golden/make_full_size_optima.py [workload@seed ...]
 
@@ -36,12 +38,13 @@ import qpgen  # noqa: E402
 from oracle import admm, checks  # noqa: E402
 
 OUT = os.path.join(HERE, "full_size_optima.json")
+XSTAR = os.path.join(HERE, "full_size_xstar.npz")
 WORKLOADS = ["random_100x1000@%d" % k for k in range(10)] + ["lasso_1000x100000@0", "portfolio_100000x1000@0",
                                                              "random_20000x200000@0"]
 TIGHT = 1e-7
 
 
-def one(key: str) -> dict:
+def one(key: str, xstar: dict) -> dict:
     name, seed = key.split("@")
     qp = qpgen.by_name(name, int(seed))
     rec = {"workload": name, "seed": int(seed)}
@@ -55,19 +58,29 @@ def one(key: str) -> dict:
                     "y_norm1": float(np.sum(np.abs(r.y))), "rho_history": [float(p) for p in r.rho_history],
                     "kkt_rel_residual": float(r.kkt_rel_residual), "seconds": round(time.time() - t, 1)}
         print(key, tag, rec[tag], flush=True)
+        if tag == "tight":
+            xstar[key] = r.x.astype(np.float32)
     return rec
 
 
-def main(names):
-    data = {}
-    if os.path.exists(OUT):
-        with open(OUT) as f:
+def main(names, out=OUT, xout=XSTAR):
+    data, xs = {}, {}
+    if os.path.exists(out):
+        with open(out) as f:
             data = json.load(f)
+    if os.path.exists(xout):
+        with np.load(xout) as z:
+            xs = {k: z[k] for k in z.files}
     for key in names:
-        data[key] = one(key)
-        with open(OUT, "w") as f:
+        data[key] = one(key, xs)
+        with open(out, "w") as f:
             json.dump(data, f, indent=1, sort_keys=True)
+        np.savez(xout, **xs)
 
 
 if __name__ == "__main__":
-    main(sys.argv[1:] or WORKLOADS)
+    args = sys.argv[1:]
+    out, xout = OUT, XSTAR
+    if args[:1] == ["--out"]:  # separate files for runs in parallel: --out STEM workload ...
+        out, xout, args = args[1] + ".json", args[1] + ".npz", args[2:]
+    main(args or WORKLOADS, out, xout)

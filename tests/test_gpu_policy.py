@@ -1,6 +1,8 @@
 """GPU BF16 policy kernels (inference, gradient, Adam) against the FP64 CPU
 oracle.  The network is not in the paper: these pins are finite differences
 (CPU, test_oracle_pins) and this comparison."""
+import os
+
 import numpy as np
 import pytest
 
@@ -286,3 +288,39 @@ def test_overflowing_network_is_a_stall(gb):
         assert abs(dev["rho"] - ref["rho"]) <= 1e-12 * ref["rho"], (dev, ref)
         assert dev["stalls"] == ref["stalls"] and dev["fallbacks"] == ref["fallbacks"], (dev, ref)
     assert pairs[-1][0]["stalls"] >= 1 and pairs[-1][0]["fallbacks"] == len(pairs)
+
+
+# -------------------------------------------- held-out learned-policy workload --
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "full_size_optima.json")
+
+
+@pytest.mark.parametrize("seed", [200000, 200001, 200002])
+def test_learned_policy_on_held_out_random_5000x50000(gb, seed):
+    """The first seeds of the held-out evaluation (n = 5000, m = 50000): the
+    learned FP32 solve reaches the eps = 1e-3 rule on the unscaled data, and
+    its objective is judged against the FP64 oracle's optimum (committed by
+    tests/golden/make_full_size_optima.py): within the convexity bound, and
+    within 1e-3 relative where the oracle's own 1e-3 solve is."""
+    import json
+    from oracle import admm, checks
+    key = f"random_5000x50000@{seed}"
+    with open(GOLDEN) as f:
+        gold = json.load(f).get(key)
+    if gold is None:
+        pytest.skip(f"no oracle optimum committed for {key}")
+    qp = qpgen.by_name("random_5000x50000", seed)
+    flat = gb.load_policy(os.path.join(os.path.dirname(gb.__file__), "policy", "rho_policy.bin"))
+    with gb.Solver(qp, precision=gb.FP32, rho_policy=gb.RHO_LEARNED, policy_params=flat) as s:
+        st = s.solve()
+        x, y, z = s.solution()
+        info = s.info()
+    assert st == gb.SOLVED, info
+    v = checks.kkt_violation(qp, x, z, y)
+    assert v.prim <= info["eps_prim"] * (1 + 1e-6) + 1e-12 and v.dual <= info["eps_dual"] * (1 + 1e-6) + 1e-12
+    t = gold["tight"]
+    f = admm.objective(qp.P, qp.q, x)
+    bound = max(float(np.sum(np.abs(y))), t["y_norm1"]) * v.prim + v.dual * (float(np.sum(np.abs(x))) + t["x_norm1"])
+    assert abs(f - t["obj"]) <= 1.001 * bound + 1e-9 * max(1.0, abs(t["obj"])), (f, t["obj"], bound)
+    if abs(gold["eps_1e-3"]["obj"] - t["obj"]) <= 1e-3 * max(1.0, abs(t["obj"])):
+        assert abs(f - t["obj"]) <= 1e-3 * max(1.0, abs(t["obj"])), (f, t["obj"])
