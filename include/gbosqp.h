@@ -17,7 +17,7 @@
  * Conventions shared by every call:
  *   - Matrices are CSR with 64-bit row pointers and 32-bit column indices,
  *     zero-based, columns strictly increasing within each row (no
- *     duplicates), values double.  Internally nnz must be < 2^31 - 64 per
+ *     duplicates), values double.  Internally nnz must be < 2^31 - 256 per
  *     matrix (also for the full P and for [P A'], which osqp_setup builds).
  *   - Bounds with |v| >= GBOSQP_INFINITY (or +-inf) are infinite.  l <= u.
  *   - Unless a call says otherwise, vector arguments are host pointers to
@@ -54,7 +54,7 @@ extern "C" {
                                          the kernels have no spin-waits; CTAs
                                          combine results by last-arriver
                                          tickets, never by waiting)           */
-#define GBOSQP_ERR_UNSUPPORTED (-9)   /* e.g. nnz >= 2^31 - 64, no sm_103a */
+#define GBOSQP_ERR_UNSUPPORTED (-9)   /* e.g. nnz >= 2^31 - 256, no sm_103a */
 #define GBOSQP_ERR_POLICY (-10)       /* learned policy parameters invalid    */
 
 /* ---- solve status (positive) ------------------------------------------ */
@@ -206,8 +206,8 @@ int gbosqp_default_settings(gbosqp_settings *s);
  * equilibration (Algorithm 2) on the device, compute the Jacobi
  * preconditioner data (Section 5.3.1), and build the solve graph.
  * P: n x n (upper triangle or full, see P_is_upper), A: m x n, q: n, l, u: m,
- * with n >= 1, m >= 0 and n + m < 2^31 - 64 (GBOSQP_ERR_UNSUPPORTED otherwise,
- * as for nnz >= 2^31 - 64 in one matrix, or nnz >= 2^30 - 32 in an upper-triangular P,
+ * with n >= 1, m >= 0 and n + m < 2^31 - 256 (GBOSQP_ERR_UNSUPPORTED otherwise,
+ * as for nnz >= 2^31 - 256 in one matrix, or nnz >= 2^30 - 128 in an upper-triangular P,
  * whose full form is built with 32-bit offsets): m = 0 is a problem without constraints (A has no
  * rows; l and u must still be non-NULL but no element is read), and P may
  * have no nonzeros (a linear program).

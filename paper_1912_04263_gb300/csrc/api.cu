@@ -124,14 +124,15 @@ int osqp_setup(gbosqp_handle **out, const gbosqp_csr *P, const gbosqp_csr *A, co
     if (n <= 0 || P->ncols != n) return bad(GBOSQP_ERR_DIMENSION, "P must be n x n with n > 0");
     if (m < 0 || A->ncols != n) return bad(GBOSQP_ERR_DIMENSION, "A must be m x n");
     if (P->nnz < 0 || A->nnz < 0) return bad(GBOSQP_ERR_CSR, "negative nnz");
-    // offsets into the matrix arrays are 32-bit ints; 64 below 2^31 leaves headroom at the arrays' ends
-    if (P->nnz >= (1LL << 31) - 64 || A->nnz >= (1LL << 31) - 64)
-        return bad(GBOSQP_ERR_UNSUPPORTED, "2^31 - 64 or more nonzeros in one matrix");
-    if (s.P_is_upper && 2 * P->nnz >= (1LL << 31) - 64)  // the full P has at most twice the upper triangle's entries
+    // offsets into the matrix arrays are 32-bit ints; 256 below 2^31 leaves room for the SpMV's
+    // whole-batch loads past the last nonzero (up to 127 elements) and for offset arithmetic
+    if (P->nnz >= (1LL << 31) - 256 || A->nnz >= (1LL << 31) - 256)
+        return bad(GBOSQP_ERR_UNSUPPORTED, "2^31 - 256 or more nonzeros in one matrix");
+    if (s.P_is_upper && 2 * P->nnz >= (1LL << 31) - 256)  // the full P has at most twice the upper triangle's entries
         return bad(GBOSQP_ERR_UNSUPPORTED,
-                   "an upper-triangular P must have fewer than 2^30 - 32 nonzeros (its full form uses 32-bit offsets)");
-    if ((int64_t)n + (int64_t)m >= (1LL << 31) - 64)
-        return bad(GBOSQP_ERR_UNSUPPORTED, "n + m must be below 2^31 - 64 (the columns of [P A'] and the joint vectors)");
+                   "an upper-triangular P must have fewer than 2^30 - 128 nonzeros (its full form uses 32-bit offsets)");
+    if ((int64_t)n + (int64_t)m >= (1LL << 31) - 256)
+        return bad(GBOSQP_ERR_UNSUPPORTED, "n + m must be below 2^31 - 256 (the columns of [P A'] and the joint vectors)");
     if (!P->rowptr || (P->nnz && (!P->colind || !P->val)) || !A->rowptr || (A->nnz && (!A->colind || !A->val)))
         return bad(GBOSQP_ERR_INVALID_ARG, "NULL CSR array");
     std::unique_ptr<gbosqp_handle> h(new gbosqp_handle());

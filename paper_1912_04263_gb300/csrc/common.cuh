@@ -89,10 +89,11 @@ constexpr int kThreads = 256;             // CTA size of every kernel of the sol
 constexpr int kWarps = kThreads / 32;
 constexpr double kInf = 1e20;             // |bound| >= kInf is infinite
 // Zeroed elements after the last nonzero of every matrix array the SpMV
-// kernels read: a warp's first and last 32-element steps may load up to 31
-// elements past its range (their products are discarded), and a zero
-// column index keeps the discarded lanes' gathers in bounds.
-constexpr int kSlack = 32;
+// kernels read: a warp loads whole batches of 4 steps of 32 elements, so it
+// may load up to 127 elements past its range (those products are
+// discarded), and a zero column index keeps the discarded lanes' gathers in
+// bounds.
+constexpr int kSlack = 128;
 
 // ------------------------------------------------------------ status block
 

@@ -729,8 +729,8 @@ SetupData device_setup(const gbosqp_csr &P, const gbosqp_csr &A, const double *q
 
     // ---- 4. [P A'], Jacobi data, q norms
     sd.nnzPAt = Pf.nnz + At.nnz;
-    if (sd.nnzPAt >= (1LL << 31) - 64 || A.nnz >= (1LL << 31) - 64)
-        fail(GBOSQP_ERR_UNSUPPORTED, "2^31 - 64 or more nonzeros in A or [P A']");
+    if (sd.nnzPAt >= (1LL << 31) - 256 || A.nnz >= (1LL << 31) - 256)
+        fail(GBOSQP_ERR_UNSUPPORTED, "2^31 - 256 or more nonzeros in A or [P A']");
     sd.PAt_rowptr.alloc((size_t)(n + 1) * sizeof(int));
     sd.PAt_pend.alloc((size_t)std::max(n, 1) * sizeof(int));
     // kSlack zeroed elements past the last nonzero, as in the copy of A

@@ -225,6 +225,7 @@ __device__ __forceinline__ void stream_item(const CsrW<T> &M, const WItem &it, c
     const int *pc = M.col + base + lane;
     T va[U], vb[U];
     int ca[U], cb[U];
+#if GB_PREDICATED_LOADS
     // steps at or past nsteps are not loaded (their lanes gather entry 0 and
     // are never summed): only the item's own steps, which reach at most 31
     // elements past it, touch the matrix arrays
@@ -240,6 +241,20 @@ __device__ __forceinline__ void stream_item(const CsrW<T> &M, const WItem &it, c
             }
         }
     };
+#else
+    // a batch that starts inside the item is loaded whole: its last step may
+    // end up to 32 U - 1 elements past the item, inside the arrays' zeroed
+    // slack (kSlack >= 32 U) or other rows' nonzeros, so every loaded column
+    // is a valid index; steps past nsteps are never summed
+    static_assert(32 * U <= kSlack, "the matrix arrays' slack must hold a whole batch");
+    auto load = [&](int s0, T(&v)[U], int(&c)[U]) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            v[u] = __ldcs(pv + ((s0 + u) << 5));
+            c[u] = __ldcs(pc + ((s0 + u) << 5));
+        }
+    };
+#endif
     // add the products of the U steps from s0 to their rows
     auto sum_batch = [&](int s0, T(&pr)[U]) {
 #pragma unroll

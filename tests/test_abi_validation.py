@@ -48,7 +48,7 @@ def _csr(base, **kw):
     ("A", dict(nrows=-1), "ERR_DIMENSION", "m x n"),
     ("P", dict(nnz=-3), "ERR_CSR", "negative nnz"),
     ("A", dict(nnz=1 << 31), "ERR_UNSUPPORTED", "2^31"),
-    ("A", dict(nnz=(1 << 31) - 64), "ERR_UNSUPPORTED", "2^31 - 64"),
+    ("A", dict(nnz=(1 << 31) - 256), "ERR_UNSUPPORTED", "2^31 - 256"),
     ("P", dict(rowptr=None), "ERR_INVALID_ARG", "NULL CSR"),
     ("A", dict(colind=None), "ERR_INVALID_ARG", "NULL CSR"),
     ("A", dict(val=None), "ERR_INVALID_ARG", "NULL CSR"),
@@ -65,7 +65,7 @@ def test_malformed_problems_are_refused_on_the_host(lib, parts, which, change, c
 
 def test_too_many_variables_and_constraints_are_refused(lib):
     """[P A'] has n + m columns and the joint vectors n + m entries, all
-    indexed with 32-bit integers: n + m must stay below 2^31 - 64.  The
+    indexed with 32-bit integers: n + m must stay below 2^31 - 256.  The
     arrays are not read before the sizes are checked."""
     n, m = 1_200_000_000, 1_000_000_000
     rp = np.zeros(2, np.int64)
@@ -78,7 +78,7 @@ def test_too_many_variables_and_constraints_are_refused(lib):
 
 def test_an_upper_triangle_whose_full_form_could_overflow_is_refused(lib):
     """The full P built from an upper triangle has up to twice its
-    nonzeros, with 32-bit offsets: an upper triangle of 2^30 - 32 or more
+    nonzeros, with 32-bit offsets: an upper triangle of 2^30 - 128 or more
     nonzeros is refused before any array is read."""
     rp = np.zeros(2, np.int64)
     v = np.zeros(1)
