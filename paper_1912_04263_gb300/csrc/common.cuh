@@ -204,6 +204,33 @@ __device__ __forceinline__ void block_reduce(Red<NS, NM> &red) {
     __syncthreads();
 }
 
+// Adds records b = threadIdx.x, threadIdx.x + blockDim.x, ... (b < count)
+// of a table of FP64 records (stride doubles apart; RS sums then RM maxima
+// each) into acc, in that order.  The loads of kLd records are issued
+// before their sums, so the last CTA of a grid reduction waits for about
+// one L2 round trip per kLd records instead of one per record.
+template <int NS, int NM, int RS, int RM>
+__device__ __forceinline__ void add_records(Red<NS, NM> &acc, const double *tab, int stride, int count) {
+    static_assert(RS <= NS && RM <= NM, "record wider than the reduction");
+    constexpr int kLd = 4, RR = RS + RM > 0 ? RS + RM : 1;
+    for (int b0 = threadIdx.x; b0 < count; b0 += kLd * blockDim.x) {
+        double v[kLd][RR];
+#pragma unroll
+        for (int u = 0; u < kLd; ++u) {
+            const int b = b0 + u * (int)blockDim.x;
+#pragma unroll
+            for (int i = 0; i < RS + RM; ++i) v[u][i] = b < count ? __ldcg(tab + (size_t)b * stride + i) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kLd; ++u) {
+#pragma unroll
+            for (int i = 0; i < RS; ++i) acc.s[i] += v[u][i];
+#pragma unroll
+            for (int i = 0; i < RM; ++i) acc.m[i] = amax(acc.m[i], v[u][RS + i]);
+        }
+    }
+}
+
 // Per-CTA partials -> the last CTA to arrive sums them in CTA order and
 // calls fin(total) with every thread of that CTA (thread 0 holds nothing
 // special; the total is broadcast through shared memory).
@@ -228,12 +255,7 @@ __device__ __forceinline__ void grid_finish(Red<NS, NM> &red, double *partials, 
     __threadfence();
     Red<NS, NM> acc;
     acc.zero();
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-#pragma unroll
-        for (int i = 0; i < NS; ++i) acc.s[i] += __ldcg(partials + (size_t)b * NR + i);
-#pragma unroll
-        for (int i = 0; i < NM; ++i) acc.m[i] = amax(acc.m[i], __ldcg(partials + (size_t)b * NR + NS + i));
-    }
+    add_records<NS, NM, NS, NM>(acc, partials, NR, (int)gridDim.x);
     block_reduce<NS, NM>(acc);
     if (threadIdx.x == 0) {
 #pragma unroll

@@ -90,6 +90,15 @@ __device__ __forceinline__ double fma_rn(double a, double b, double c) { return 
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 
+// Where the plan of k_pcg_kp keeps the rows it cut between warps: the
+// split-row index of every row (-1 when whole), the split rows and their
+// parts' sums, which k_pcg_update adds into Kp.
+struct KpParts {
+    const int *split_of;
+    const SplitRow *split;
+    const double *split_part;
+};
+
 template <class T>
 struct Vecs {
     T *xy, *xt, *pt, *dxy;
@@ -113,6 +122,13 @@ struct Vecs {
 constexpr int kMinBlocks = GB_MIN_BLOCKS;
 // steps of 32 nonzeros per batch of the warp-stream SpMV (see spmv.cuh)
 constexpr int kU = 4;
+// plan cost of a row of the group path, in nonzeros (measured on GB300 on
+// the Lasso [P A']: at a weight of 24, the warps holding its 101000 rows of
+// two nonzeros finished their share in under a third of the time the warps
+// of its long rows took)
+#ifndef GB_GROUP_ROW
+#define GB_GROUP_ROW 8
+#endif
 // rows longer than this go to CTA bundles in the warp-stream plan
 #ifndef GB_BUNDLE_MIN
 #define GB_BUNDLE_MIN 4096
@@ -271,9 +287,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : 2) k_p
     warp_rows<kU, T, false>(A, GatherDir<T>{v.ypc, beta}, epi, red);
 }
 
-// Kp = P p + sigma p + A' t;  p'Kp
+// Kp = P p + sigma p + A' t;  p'Kp.  A row cut between warps contributes
+// by parts: p_i (part sum) to p'Kp from each part and p_i sigma p_i from
+// the part holding the row's start; its Kp entry is formed from the parts
+// by k_pcg_update, the one reader of Kp.  So no warp waits on the others'
+// parts and the kernel's end is not held up by a chain of combining warps.
 template <class T>
 struct EpiKp {
+    static constexpr bool kSplitParts = true;
     Vecs<T> v;
     T sigma;
     __device__ __forceinline__ void row(int i, T s1, T, Red<1, 0> &red) {
@@ -281,6 +302,11 @@ struct EpiKp {
         const T kp = s1 + sigma * p;
         v.kp[i] = kp;
         red.s[0] += (double)p * (double)kp;
+    }
+    __device__ __forceinline__ void part(int i, bool first, T s1, T, Red<1, 0> &red) {
+        const T p = v.pt[i];
+        red.s[0] += (double)p * (double)s1;
+        if (first) red.s[0] += (double)p * (double)(sigma * p);
     }
 };
 
@@ -301,23 +327,49 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : 2) k_p
             st->breakdown = 1;
         }
     };
-    grid_finish_w<1, 0>(red, PAt, partials, &st->tickets[kTkK2], fin);
+    grid_finish_w<1, 0, false>(red, PAt, partials, &st->tickets[kTkK2], fin);
 }
 
 // x~ += a p; r += a Kp; yv = M^{-1} r; p_prev = p; r'yv; ||r||_inf; beta.
 // The vector updates run in the working precision; r'yv accumulates the
 // exact products in FP64.
+// Kp_i of a row that k_pcg_kp's plan cut between warps: its parts' sums
+// (FP64, slot order) rounded to T, plus sigma p_i, as EpiKp::row forms it.
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_pcg_update(Vecs<T> v, Status *st, double *partials,
+__device__ __forceinline__ T kp_from_parts(const SplitRow &S, const double *split_part, T sigma, T p) {
+    constexpr int kLd = 8;
+    double s = 0.0;
+    for (int k0 = 0; k0 < S.nparts; k0 += kLd) {
+        double v[kLd];
+#pragma unroll
+        for (int u = 0; u < kLd; ++u) v[u] = k0 + u < S.nparts ? __ldcg(split_part + 2 * (size_t)(S.slot0 + k0 + u)) : 0.0;
+#pragma unroll
+        for (int u = 0; u < kLd; ++u)
+            if (k0 + u < S.nparts) s += v[u];
+    }
+    return T(s) + sigma * p;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_pcg_update(Vecs<T> v, Status *st, double *partials, KpParts kpp,
                                                          cudaGraphConditionalHandle hP, int use_h) {
     const T a = T(st->alpha_cg);
+    const T sigma = T(st->sigma);
     const int n = v.n;
     Red<1, 1> red;
     red.zero();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const T p = v.pt[i];
         const T x = v.xt[i] + a * p;
-        const T r = v.r[i] + a * v.kp[i];
+        T kp;
+        const int l = kpp.split_of[i];
+        if (l < 0) {
+            kp = v.kp[i];
+        } else {
+            kp = kp_from_parts<T>(kpp.split[l], kpp.split_part, sigma, p);
+            v.kp[i] = kp;
+        }
+        const T r = v.r[i] + a * kp;
         const T y = v.minv[i] * r;
         v.xt[i] = x;
         v.r[i] = r;
@@ -1429,7 +1481,7 @@ public:
             switch (kernel) {
                 case GBOSQP_K_PCG_DIRECTION: launch_smem(k_pcg_p_t<T>, gPt_, kThreads, kSmemT, stream_, csrA(gPt_), v, (const Status *)st); break;
                 case GBOSQP_K_PCG_KAPPLY: launch_smem(k_pcg_kp<T>, gKp_, kThreads, kSmemT, stream_, csrPAt(gKp_), v, st, partials_.as<double>()); break;
-                case GBOSQP_K_PCG_UPDATE: launch(k_pcg_update<T>, gridVec_, kThreads, stream_, v, st, partials_.as<double>(), (cudaGraphConditionalHandle)0, 0); break;
+                case GBOSQP_K_PCG_UPDATE: launch(k_pcg_update<T>, gridVec_, kThreads, stream_, v, st, partials_.as<double>(), kp_parts(), (cudaGraphConditionalHandle)0, 0); break;
                 case GBOSQP_K_PCG_INIT: launch_smem(k_pcg_init<T>, gInit_, kThreads, kSmemT, stream_, csrPAt(gInit_), v, st, partials_.as<double>(), (cudaGraphConditionalHandle)0, 0); break;
                 case GBOSQP_K_ADMM_UPDATE: launch_smem(k_admm_update<T>, gAdmm_, kThreads, kSmemT, stream_, csrA(gAdmm_), v, st); break;
                 case GBOSQP_K_CHECK_A: launch_smem(k_check_a<T>, gCa_, kThreads, kSmemD, stream_, csrA(gCa_), v, st, partials_.as<double>()); break;
@@ -1537,7 +1589,7 @@ private:
     struct WDev {
         DevBuf meta, scratch;
         int nwarps = 0, nsplit = 0;
-        size_t off_wpart = 0, off_wsplit = 0, off_split = 0;  // in meta
+        size_t off_wpart = 0, off_wsplit = 0, off_split = 0, off_split_of = 0;  // in meta
         size_t off_part = 0, off_red = 0, scratch_bytes = 0;  // in scratch
     };
     struct MatPlans {
@@ -1559,6 +1611,7 @@ private:
     static WPlanHost host_plan(const MatPlans &mp, int grid) {
         WPlanCost cost;
         cost.bundle_min = kBundleMin;
+        cost.group_row = GB_GROUP_ROW;
         return build_wplan(mp.rp, grid * kWWarps, cost);
     }
 
@@ -1591,12 +1644,19 @@ private:
         d.off_wpart = up16(sizeof(WItem) * hp.items.size());
         d.off_wsplit = d.off_wpart + up16(sizeof(int) * hp.wpart.size());
         d.off_split = d.off_wsplit + up16(sizeof(WSplit) * hp.wsplit.size());
-        const size_t meta_bytes = d.off_split + up16(sizeof(SplitRow) * hp.split.size());
+        d.off_split_of = d.off_split + up16(sizeof(SplitRow) * hp.split.size());
+        const int nrows = (int)mp.rp.size() - 1;
+        const size_t meta_bytes = d.off_split_of + up16(sizeof(int) * std::max(nrows, 1));
         std::vector<unsigned char> h(meta_bytes, 0);
         if (!hp.items.empty()) std::memcpy(h.data(), hp.items.data(), sizeof(WItem) * hp.items.size());
         std::memcpy(h.data() + d.off_wpart, hp.wpart.data(), sizeof(int) * hp.wpart.size());
         std::memcpy(h.data() + d.off_wsplit, hp.wsplit.data(), sizeof(WSplit) * hp.wsplit.size());
         if (!hp.split.empty()) std::memcpy(h.data() + d.off_split, hp.split.data(), sizeof(SplitRow) * hp.split.size());
+        {
+            int *so = reinterpret_cast<int *>(h.data() + d.off_split_of);
+            std::fill(so, so + std::max(nrows, 1), -1);
+            for (size_t l = 0; l < hp.split.size(); ++l) so[hp.split[l].row] = (int)l;
+        }
         d.meta.alloc(meta_bytes);
         // pageable source: the copy is staged before the call returns
         GB_CUDA(cudaMemcpyAsync(d.meta.p, h.data(), meta_bytes, cudaMemcpyHostToDevice, stream_));
@@ -1628,6 +1688,7 @@ private:
         M.split_count = reinterpret_cast<int *>(scr);
         M.split_part = reinterpret_cast<double *>(scr + pd.off_part);
         M.split_red = reinterpret_cast<double *>(scr + pd.off_red);
+        M.split_of = reinterpret_cast<const int *>(meta + pd.off_split_of);
         return M;
     }
     // CTAs of a warp-stream kernel: as many as fit at once, fewer when the
@@ -1651,6 +1712,10 @@ private:
 
     CsrW<T> csrA(int grid) const { return csr(matA_, A_val_.as<T>(), grid); }
     CsrW<T> csrPAt(int grid) const { return csr(matPAt_, PAt_val_.as<T>(), grid); }
+    KpParts kp_parts() const {
+        const CsrW<T> M = csrPAt(gKp_);
+        return KpParts{M.split_of, M.split, M.split_part};
+    }
 
     Vecs<T> vecs() const {
         Vecs<T> v;
@@ -1715,7 +1780,7 @@ private:
         }
         launch_smem(k_pcg_p_t<T>, gPt_, kThreads, kSmemT, stream_, csrA(gPt_), v, st);
         launch_smem(k_pcg_kp<T>, gKp_, kThreads, kSmemT, stream_, csrPAt(gKp_), v, st, partials_.as<double>());
-        launch(k_pcg_update<T>, gridVec_, kThreads, stream_, v, st, partials_.as<double>(), h, use_h);
+        launch(k_pcg_update<T>, gridVec_, kThreads, stream_, v, st, partials_.as<double>(), kp_parts(), h, use_h);
         GB_CUDA(cudaGetLastError());
     }
     void launch_admm(const Vecs<T> &v, Status *st) {
@@ -1783,7 +1848,7 @@ private:
             } else {
                 cudaGraphNode_t a = add_kernel_smem(pbody, nullptr, k_pcg_p_t<T>, gPt_, kSmemT, csrA(gPt_), v, (const Status *)st);
                 cudaGraphNode_t b = add_kernel_smem(pbody, &a, k_pcg_kp<T>, gKp_, kSmemT, csrPAt(gKp_), v, st, part);
-                add_kernel(pbody, &b, k_pcg_update<T>, gridVec_, v, st, part, hP, 1);
+                add_kernel(pbody, &b, k_pcg_update<T>, gridVec_, v, st, part, kp_parts(), hP, 1);
             }
             prev = add_kernel_smem(body, &nw, k_admm_update<T>, gAdmm_, kSmemT, csrA(gAdmm_), v, st);
         }

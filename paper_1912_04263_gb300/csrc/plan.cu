@@ -3,12 +3,16 @@
 // and the table of rows cut between warps.
 //
 // Rows longer than bundle_min (when set) are taken out of the contiguous
-// cut and put into bundles of kWWarps consecutive long rows; a bundle gets
-// a run of CTAs, and the q-th of its k CTAs gives warp j the q-th of k
-// equal nonzero fractions of the bundle's j-th row.  The warps of a CTA
-// then sweep the same fraction of their rows side by side, which for rows
-// with similarly spread columns keeps the gathered entries shared in the
-// CTA's L1.  The other rows are cut contiguously over the remaining warps.
+// cut and put into bundles of kWWarps consecutive long rows.  The bundles
+// share a run of CTAs in proportion to their longest rows, continuously: CTA
+// c takes the same weight range [B_c, B_(c+1)) of the bundles' total, which
+// may end inside one bundle and go on into the next, and warp j of the CTA
+// takes, of row j of every bundle its range touches, the part that range
+// covers.  The warps of a CTA then sweep the same column window of their
+// rows side by side, which for rows with similarly spread columns keeps the
+// gathered entries shared in the CTA's L1, and every CTA gets the same
+// amount of work.  The other rows are cut contiguously over the remaining
+// warps.
 #include <algorithm>
 #include <vector>
 
@@ -70,24 +74,16 @@ WPlanHost build_wplan(const std::vector<int> &rp, int nwarps, const WPlanCost &c
     const int nb = (int)(brows.size() + kWWarps - 1) / kWWarps;
     std::vector<char> bundled(nrows > 0 ? nrows : 1, 0);
     for (int r : brows) bundled[r] = 1;
-    // CTAs of bundle b: [bcta[b], bcta[b+1]), in proportion to its longest row
-    std::vector<int> bcta(nb + 1, 0);
-    if (nb > 0) {
-        std::vector<long long> wpre(nb + 1, 0);
-        for (int b = 0; b < nb; ++b) {
-            long long mx = 0;
-            for (int j = 0; j < kWWarps && b * kWWarps + j < (int)brows.size(); ++j)
-                mx = std::max(mx, row_cost(len_of(brows[b * kWWarps + j])));
-            wpre[b + 1] = wpre[b] + mx;
-        }
-        for (int b = 1; b < nb; ++b) {
-            int c = (int)((double)cta_b * wpre[b] / std::max(wpre[nb], 1LL) + 0.5);
-            c = std::max(c, bcta[b - 1] + 1);
-            c = std::min(c, cta_b - (nb - b));
-            bcta[b] = c;
-        }
-        bcta[nb] = cta_b;
+    // weight of bundle b: its longest row; prefix wpre, CTA c's range
+    // [bound(c), bound(c + 1)) of the total
+    std::vector<long long> wpre(nb + 1, 0);
+    for (int b = 0; b < nb; ++b) {
+        long long mx = 0;
+        for (int j = 0; j < kWWarps && b * kWWarps + j < (int)brows.size(); ++j)
+            mx = std::max(mx, row_cost(len_of(brows[b * kWWarps + j])));
+        wpre[b + 1] = wpre[b] + std::max(mx, 1LL);
     }
+    auto bound = [&](int c) -> long long { return cta_b > 0 ? wpre[nb] * c / cta_b : 0; };
 
     // contiguous cut of the other rows over warps [wb, nwarps); a cut may
     // fall inside a row longer than split_min, at a nonzero index rounded to
@@ -123,39 +119,45 @@ WPlanHost build_wplan(const std::vector<int> &rp, int nwarps, const WPlanCost &c
     }
     auto interior = [&](const Cut &c) { return c.r < nrows && c.k > rp[c.r]; };
 
-    // bundled warp ranges: warp j of the q-th of the k CTAs of bundle b
-    auto frac = [&](int r, long long q, long long k) -> int {
-        if (q <= 0) return rp[r];
-        if (q >= k) return rp[r + 1];
-        long long e = rp[r] + (long long)len_of(r) * q / k;
+    // the element of row r of bundle b at weight B: the same rounding for
+    // the two CTAs that share a boundary, so the parts tile the row
+    auto cutp = [&](int r, int b, long long B) -> int {
+        if (B <= wpre[b]) return rp[r];
+        if (B >= wpre[b + 1]) return rp[r + 1];
+        long long e = rp[r] + (long long)len_of(r) * (B - wpre[b]) / (wpre[b + 1] - wpre[b]);
         e = ((e + 16) / 32) * 32;
         return (int)std::min<long long>(std::max<long long>(e, rp[r]), rp[r + 1]);
     };
-    auto brange = [&](int w, int &row, int &lo, int &hi) -> bool {
-        const int c = w / kWWarps, j = w % kWWarps;
-        const int b = (int)(std::upper_bound(bcta.begin(), bcta.end(), c) - bcta.begin()) - 1;
-        if (b * kWWarps + j >= (int)brows.size()) return false;
-        row = brows[b * kWWarps + j];
-        const int q = c - bcta[b], k = bcta[b + 1] - bcta[b];
-        lo = frac(row, q, k);
-        hi = frac(row, q + 1, k);
-        return lo < hi;
+    // the non-empty parts of bundle warp w, in row order: (row, lo, hi)
+    struct Part {
+        int r, lo, hi;
     };
+    auto bparts = [&](int w, std::vector<Part> &out) {
+        out.clear();
+        const int c = w / kWWarps, j = w % kWWarps;
+        const long long B0 = bound(c), B1 = bound(c + 1);
+        if (B0 >= B1) return;
+        int b = (int)(std::upper_bound(wpre.begin(), wpre.end(), B0) - wpre.begin()) - 1;
+        for (; b < nb && wpre[b] < B1; ++b) {
+            if (b * kWWarps + j >= (int)brows.size()) continue;
+            const int r = brows[b * kWWarps + j];
+            const int lo = cutp(r, b, B0), hi = cutp(r, b, B1);
+            if (lo < hi) out.push_back(Part{r, lo, hi});
+        }
+    };
+    std::vector<Part> parts;
+    std::vector<int> npieces(nrows > 0 ? nrows : 1, 0);
+    for (int w = 0; w < cta_b * kWWarps; ++w) {
+        bparts(w, parts);
+        for (const Part &q : parts) ++npieces[q.r];
+    }
 
     // rows cut between warps, in row order
     std::vector<int> split_rows;
     for (int w = 1; w < nw; ++w)
         if (interior(cut[w]) && (split_rows.empty() || split_rows.back() != cut[w].r)) split_rows.push_back(cut[w].r);
-    for (int b = 0; b < nb; ++b) {
-        const int k = bcta[b + 1] - bcta[b];
-        for (int j = 0; j < kWWarps && b * kWWarps + j < (int)brows.size(); ++j) {
-            // split when at least two of its fractions are non-empty
-            const int r = brows[b * kWWarps + j];
-            int parts = 0;
-            for (int q = 0; q < k; ++q) parts += frac(r, q, k) < frac(r, q + 1, k);
-            if (parts >= 2) split_rows.push_back(r);
-        }
-    }
+    for (int r : brows)
+        if (npieces[r] >= 2) split_rows.push_back(r);
     std::sort(split_rows.begin(), split_rows.end());
     std::vector<int> sid(nrows > 0 ? nrows : 1, -1);
     for (size_t l = 0; l < split_rows.size(); ++l) sid[split_rows[l]] = (int)l;
@@ -166,11 +168,16 @@ WPlanHost build_wplan(const std::vector<int> &rp, int nwarps, const WPlanCost &c
     std::vector<int> nparts(split_rows.size(), 0);
     for (int w = 0; w < wb; ++w) {
         P.wpart[w] = (int)P.items.size();
-        int row, lo, hi;
-        if (!brange(w, row, lo, hi)) continue;
-        const int h = id_of(row);
-        if (h >= 0) P.wsplit[w].head = h, ++nparts[h];
-        P.items.push_back(WItem{row, row + 1, lo, hi});
+        bparts(w, parts);
+        for (const Part &q : parts) {
+            const int h = id_of(q.r);
+            if (h >= 0) {  // at most two: a part of a bundle inside the range is not split
+                if (P.wsplit[w].head < 0) P.wsplit[w].head = h;
+                else P.wsplit[w].tail = h;
+                ++nparts[h];
+            }
+            P.items.push_back(WItem{q.r, q.r + 1, q.lo, q.hi});
+        }
     }
     for (int v = 0; v < nw; ++v) {
         const int w = wb + v;

@@ -25,6 +25,8 @@
 // point pend is given; otherwise s2 = 0) and adds to the warp's reduction.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace gb {
@@ -72,6 +74,7 @@ struct CsrW {
     int *split_count = nullptr;       // one ticket per split row, zero between launches
     double *split_part = nullptr;     // 2 sums per slot
     double *split_red = nullptr;      // kMaxSplitSums epilogue sums per split row
+    const int *split_of = nullptr;    // per row: its index in split, or -1
 };
 
 // ------------------------------------------------------------ host plan
@@ -160,6 +163,32 @@ __device__ __forceinline__ void publish_part(const CsrW<T> &M, int l, int slot, 
     (void)last;
 }
 
+// An epilogue whose split rows contribute linearly (Epi::kSplitParts) takes
+// each part of a split row by itself: the core stores the part's sums in
+// its slot, and epi.part(row, first, s1, s2, red) adds what the part
+// contributes to the warp's reduction (first: the part holding the row's
+// start); a later kernel forms the row's value from the slots, in slot
+// order.  Such a kernel needs no ticket, fence or combining warp.
+template <class E, class = void>
+struct SplitParts : std::false_type {};
+template <class E>
+struct SplitParts<E, std::void_t<decltype(E::kSplitParts)>> : std::integral_constant<bool, E::kSplitParts> {};
+
+// One warp's part of split row l, in slot `slot`.
+template <class Acc, class T, class Epi, class RedT>
+__device__ __forceinline__ void split_part(const CsrW<T> &M, int l, int slot, int row, Acc t1, Acc t2, Epi &epi,
+                                           RedT &red) {
+    if constexpr (SplitParts<Epi>::value) {
+        if ((threadIdx.x & 31) == 0) {
+            M.split_part[2 * (size_t)slot] = (double)t1;
+            M.split_part[2 * (size_t)slot + 1] = (double)t2;
+            epi.part(row, slot == M.split[l].slot0, t1, t2, red);
+        }
+    } else {
+        publish_part<Acc>(M, l, slot, row, t1, t2, epi, red);
+    }
+}
+
 }  // namespace wdetail
 
 // Stream item: rows [it.r0, it.r1), nonzeros [it.k0, it.k1), each row
@@ -209,8 +238,8 @@ __device__ __forceinline__ void stream_item(const CsrW<T> &M, const WItem &it, c
     auto finish_row = [&](int r, Acc t1, Acc t2) {
         if (r == head_row || r == tail_row) {
             const WSplit w2 = M.wsplit[wid];  // reloaded: keeps the split ids out of the loop's registers
-            if (r == head_row) publish_part<Acc>(M, w2.head, w2.head_slot, r, t1, t2, epi, red);
-            else publish_part<Acc>(M, w2.tail, w2.tail_slot, r, t1, t2, epi, red);
+            if (r == head_row) split_part<Acc>(M, w2.head, w2.head_slot, r, t1, t2, epi, red);
+            else split_part<Acc>(M, w2.tail, w2.tail_slot, r, t1, t2, epi, red);
         } else {
             if (lane == npend) {
                 prow = r;
@@ -402,10 +431,11 @@ __device__ __forceinline__ void warp_rows(const CsrW<T> &M, const Gather &gather
     }
 }
 
-// Grid total of a warp-stream kernel's reduction: per-CTA partials and the
+// Grid total of a warp-stream kernel's reduction: per-CTA partials and (but
+// for kernels whose split rows contribute by parts, SplitRed = false) the
 // split rows' epilogue sums, added in a fixed order by the last CTA to
 // arrive, which then calls fin(total) with every thread.
-template <int NS, int NM, class T, class Fin>
+template <int NS, int NM, bool SplitRed = true, class T, class Fin>
 __device__ __forceinline__ void grid_finish_w(Red<NS, NM> &red, const CsrW<T> &M, double *partials,
                                               unsigned int *ticket, Fin &fin) {
     constexpr int NR = NS + NM;
@@ -426,19 +456,9 @@ __device__ __forceinline__ void grid_finish_w(Red<NS, NM> &red, const CsrW<T> &M
     __threadfence();
     Red<NS, NM> acc;
     acc.zero();
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-#pragma unroll
-        for (int i = 0; i < NS; ++i) acc.s[i] += __ldcg(partials + (size_t)b * NR + i);
-#pragma unroll
-        for (int i = 0; i < NM; ++i) acc.m[i] = amax(acc.m[i], __ldcg(partials + (size_t)b * NR + NS + i));
-    }
+    add_records<NS, NM, NS, NM>(acc, partials, NR, (int)gridDim.x);
     static_assert(NS <= kMaxSplitSums, "more sums than the split-row slots hold");
-    if (NS > 0) {
-        for (int l = threadIdx.x; l < M.nsplit; l += blockDim.x) {
-#pragma unroll
-            for (int i = 0; i < NS; ++i) acc.s[i] += __ldcg(M.split_red + (size_t)l * kMaxSplitSums + i);
-        }
-    }
+    if (NS > 0 && SplitRed) add_records<NS, NM, NS, 0>(acc, M.split_red, kMaxSplitSums, M.nsplit);
     block_reduce<NS, NM>(acc);
     if (threadIdx.x == 0) {
 #pragma unroll

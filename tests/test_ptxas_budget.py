@@ -22,7 +22,7 @@ CSRC = os.path.join(ROOT, "paper_1912_04263_gb300", "csrc")
 
 # kernel name fragment -> largest spill (bytes of stores) allowed
 KNOWN_SPILLS = {"k_pcg_kpIfE": 4, "k_pcg_initIfE": 32, "k_check_bIfE": 60, "k_inf_bIfE": 4, "k_spmvIffE": 36,
-                "k_sr_kapplyIfE": 48, "k_sr_directionIfE": 104}
+                "k_sr_kapplyIfE": 48, "k_sr_directionIfE": 104, "k_admm_updateIfE": 8}
 
 
 def _nvcc():
