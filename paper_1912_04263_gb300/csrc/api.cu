@@ -167,8 +167,13 @@ int osqp_setup(gbosqp_handle **out, const gbosqp_csr *P, const gbosqp_csr *A, co
         const auto t0 = std::chrono::steady_clock::now();
         const long long l0 = gb::g_launches;
         gb::PoolScope pool_scope(h->stream);
-        gb::SetupData sd = gb::device_setup(*P, *A, q, l, u, s, h->stream);
-        h->eng = gb::make_engine(std::move(sd), s, h->stream);
+        // the SpMV plans are built on host threads while the device equilibrates
+        std::shared_ptr<gb::PlanPrefetch> plans;
+        gb::SetupData sd = gb::device_setup(*P, *A, q, l, u, s, h->stream,
+                                            [&](std::vector<int> &&rpA, std::vector<int> &&rpP) {
+                                                plans = gb::start_plans(s, std::move(rpA), std::move(rpP));
+                                            });
+        h->eng = gb::make_engine(std::move(sd), s, h->stream, std::move(plans));
         GB_CUDA(cudaStreamSynchronize(h->stream));
         h->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         h->setup_launches = gb::g_launches - l0;

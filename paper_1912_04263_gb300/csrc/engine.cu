@@ -994,12 +994,108 @@ cudaGraphNode_t add_while(cudaGraph_t g, const cudaGraphNode_t *dep, cudaGraphCo
     return node;
 }
 
+// ------------------------------------------------------- launch geometry
+
+// CTAs of a warp-stream kernel over a matrix with row pointer rp: as many
+// as fit at once, fewer for small matrices (about 512 nonzeros per warp).
+int grid_for_rows(const std::vector<int> &rp, const void *kernel) {
+    int per_sm = 0;
+    GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0));
+    const long long work = (rp.empty() ? 0LL : (long long)rp.back()) + 16LL * (long long)(rp.size() - 1);
+    const long long want = (work + (long long)kWWarps * 512 - 1) / ((long long)kWWarps * 512);
+    return (int)std::max(1LL, std::min<long long>(want, (long long)device_sm_count() * std::max(per_sm, 1)));
+}
+
+// The grids of every matrix kernel of a handle in precision T.
+struct Grids {
+    int pt = 1, admm = 1, ca = 1, ia = 1, spA = 1, sr1 = 1;  // over A
+    int kp = 1, init = 1, cb = 1, ib = 1, spP = 1, sr2 = 1;  // over [P A']
+    std::vector<int> over_A(bool sr) const {
+        std::vector<int> g{pt, admm, ca, ia, spA};
+        if (sr) g.push_back(sr1);
+        return g;
+    }
+    std::vector<int> over_PAt(bool sr) const {
+        std::vector<int> g{kp, init, cb, ib, spP};
+        if (sr) g.push_back(sr2);
+        return g;
+    }
+};
+
+template <class T>
+Grids solve_grids(const std::vector<int> &rpA, const std::vector<int> &rpP, bool sr) {
+    Grids g;
+    g.pt = grid_for_rows(rpA, (const void *)k_pcg_p_t<T>);
+    g.admm = grid_for_rows(rpA, (const void *)k_admm_update<T>);
+    g.ca = grid_for_rows(rpA, (const void *)k_check_a<T>);
+    g.ia = grid_for_rows(rpA, (const void *)k_inf_a<T>);
+    g.spA = grid_for_rows(rpA, (const void *)k_spmv<T, T>);
+    g.kp = grid_for_rows(rpP, (const void *)k_pcg_kp<T>);
+    g.init = grid_for_rows(rpP, (const void *)k_pcg_init<T>);
+    g.cb = grid_for_rows(rpP, (const void *)k_check_b<T>);
+    g.ib = grid_for_rows(rpP, (const void *)k_inf_b<T>);
+    g.spP = grid_for_rows(rpP, (const void *)k_spmv<T, T>);
+    if (sr) {
+        g.sr1 = grid_for_rows(rpA, (const void *)k_sr_direction<T>);
+        g.sr2 = grid_for_rows(rpP, (const void *)k_sr_kapply<T>);
+    }
+    return g;
+}
+
+// Host plan of the warp-stream SpMV over a matrix for one grid.
+WPlanHost host_plan(const std::vector<int> &rp, int grid) {
+    WPlanCost cost;
+    cost.bundle_min = kBundleMin;
+    cost.group_row = GB_GROUP_ROW;
+    return build_wplan(rp, grid * kWWarps, cost);
+}
+
+}  // namespace
+
+// Plans started on host threads during set-up (see engine.cuh).
+struct PlanPrefetch {
+    std::vector<int> rpA, rpP;
+    std::vector<std::pair<int, int>> keys;  // (0: A, 1: [P A'], grid)
+    std::vector<std::future<WPlanHost>> fut;
+    std::vector<WPlanHost> plans;
+    void wait() {
+        for (auto &f : fut) plans.push_back(f.get());
+        fut.clear();
+    }
+    const WPlanHost *find(int mat, int grid) const {
+        for (size_t i = 0; i < plans.size(); ++i)
+            if (keys[i] == std::make_pair(mat, grid)) return &plans[i];
+        return nullptr;
+    }
+};
+
+std::shared_ptr<PlanPrefetch> start_plans(const gbosqp_settings &s, std::vector<int> &&A_rp,
+                                          std::vector<int> &&PAt_rp) {
+    auto pf = std::make_shared<PlanPrefetch>();
+    pf->rpA = std::move(A_rp);
+    pf->rpP = std::move(PAt_rp);
+    const bool sr = s.pcg_variant == GBOSQP_PCG_SINGLE_REDUCTION;
+    const Grids g = s.precision == GBOSQP_FP64 ? solve_grids<double>(pf->rpA, pf->rpP, sr)
+                                               : solve_grids<float>(pf->rpA, pf->rpP, sr);
+    for (int mat = 0; mat < 2; ++mat) {
+        const std::vector<int> &rp = mat == 0 ? pf->rpA : pf->rpP;
+        for (int grid : (mat == 0 ? g.over_A(sr) : g.over_PAt(sr))) {
+            if (std::find(pf->keys.begin(), pf->keys.end(), std::make_pair(mat, grid)) != pf->keys.end()) continue;
+            pf->keys.emplace_back(mat, grid);
+            pf->fut.push_back(std::async(std::launch::async, host_plan, std::cref(rp), grid));
+        }
+    }
+    return pf;
+}
+
+namespace {
+
 // ------------------------------------------------------------------ engine
 
 template <class T>
 class Engine final : public EngineBase {
 public:
-    Engine(SetupData &&sd, const gbosqp_settings &s, cudaStream_t stream) : s_(s), stream_(stream) {
+    Engine(SetupData &&sd, const gbosqp_settings &s, cudaStream_t stream, PlanPrefetch *pre) : s_(s), stream_(stream) {
         n = sd.n;
         m = sd.m;
         nnzA = sd.nnzA;
@@ -1016,9 +1112,10 @@ public:
         PAt_val_ = convert(std::move(sd.PAt_val), nnzPAt);
         D_ = std::move(sd.D);
         E_ = std::move(sd.E);
-        // host row pointers of the work plans
-        matA_.rp = std::move(sd.A_rowptr_host);
-        matPAt_.rp = std::move(sd.PAt_rowptr_host);
+        // host row pointers of the work plans (from the plans started during
+        // set-up, when there are some)
+        matA_.rp = pre ? std::move(pre->rpA) : std::move(sd.A_rowptr_host);
+        matPAt_.rp = pre ? std::move(pre->rpP) : std::move(sd.PAt_rowptr_host);
         // vectors
         const size_t nm = (size_t)n + m;
         xy_.alloc(sizeof(T) * std::max<size_t>(nm, 1));
@@ -1056,33 +1153,25 @@ public:
         GB_CUDA(cudaMemsetAsync(z_out_.p, 0, z_out_.bytes, stream_));
         // launch geometry and reduction scratch: each matrix kernel's grid
         // is the CTAs that fit at once, fewer for small matrices
-        gPt_ = grid_for_rows(matA_.rp, (const void *)k_pcg_p_t<T>);
-        gAdmm_ = grid_for_rows(matA_.rp, (const void *)k_admm_update<T>);
-        gCa_ = grid_for_rows(matA_.rp, (const void *)k_check_a<T>);
-        gKp_ = grid_for_rows(matPAt_.rp, (const void *)k_pcg_kp<T>);
-        gInit_ = grid_for_rows(matPAt_.rp, (const void *)k_pcg_init<T>);
-        gCb_ = grid_for_rows(matPAt_.rp, (const void *)k_check_b<T>);
-        gIa_ = grid_for_rows(matA_.rp, (const void *)k_inf_a<T>);
-        gIb_ = grid_for_rows(matPAt_.rp, (const void *)k_inf_b<T>);
+        const Grids G = solve_grids<T>(matA_.rp, matPAt_.rp, sr_);
+        gPt_ = G.pt;
+        gAdmm_ = G.admm;
+        gCa_ = G.ca;
+        gIa_ = G.ia;
+        gKp_ = G.kp;
+        gInit_ = G.init;
+        gCb_ = G.cb;
+        gIb_ = G.ib;
         if (sr_) {
-            gSr1_ = grid_for_rows(matA_.rp, (const void *)k_sr_direction<T>);
-            gSr2_ = grid_for_rows(matPAt_.rp, (const void *)k_sr_kapply<T>);
+            gSr1_ = G.sr1;
+            gSr2_ = G.sr2;
         }
         // vector kernels: about 4 elements per thread
         const int cap = device_sm_count() * 8;
         gridVec_ = std::max(1, std::min(grid_for_n(n, kThreads), cap));
         gridN_ = std::max(1, std::min(grid_for_n(std::max(n, m), kThreads * 4), cap));
         const int maxgrid = std::max({gPt_, gAdmm_, gCa_, gKp_, gInit_, gCb_, gIa_, gIb_, gridN_, gridVec_, gSr1_, gSr2_});
-        const int gSpA = grid_for_rows(matA_.rp, (const void *)k_spmv<T, T>);
-        const int gSpP = grid_for_rows(matPAt_.rp, (const void *)k_spmv<T, T>);
-        {
-            std::vector<int> gA{gPt_, gAdmm_, gCa_, gIa_, gSpA}, gP{gKp_, gInit_, gCb_, gIb_, gSpP};
-            if (sr_) {
-                gA.push_back(gSr1_);
-                gP.push_back(gSr2_);
-            }
-            build_plans(gA, gP);
-        }
+        build_plans(G.over_A(sr_), G.over_PAt(sr_), pre);
         partials_.alloc(sizeof(double) * (size_t)maxgrid * 8);
         // status block
         Status h;
@@ -1608,16 +1697,10 @@ private:
 
     // The plan of matrix mp for a launch of `grid` CTAs (built once per
     // grid size; kernels with the same grid share it).
-    static WPlanHost host_plan(const MatPlans &mp, int grid) {
-        WPlanCost cost;
-        cost.bundle_min = kBundleMin;
-        cost.group_row = GB_GROUP_ROW;
-        return build_wplan(mp.rp, grid * kWWarps, cost);
-    }
 
     // Build the host plans of all the given grids of both matrices on host
     // threads at once, then upload them (the device calls stay on this thread).
-    void build_plans(const std::vector<int> &gA, const std::vector<int> &gP) {
+    void build_plans(const std::vector<int> &gA, const std::vector<int> &gP, const PlanPrefetch *pre = nullptr) {
         std::vector<std::pair<const MatPlans *, int>> todo;
         for (int g : gA)
             if (!matA_.by_grid.count(g) && std::find(todo.begin(), todo.end(), std::make_pair((const MatPlans *)&matA_, g)) == todo.end())
@@ -1625,18 +1708,26 @@ private:
         for (int g : gP)
             if (!matPAt_.by_grid.count(g) && std::find(todo.begin(), todo.end(), std::make_pair((const MatPlans *)&matPAt_, g)) == todo.end())
                 todo.emplace_back(&matPAt_, g);
-        std::vector<std::future<WPlanHost>> fut;
-        for (auto &t : todo) fut.push_back(std::async(std::launch::async, host_plan, std::cref(*t.first), t.second));
+        std::vector<std::future<WPlanHost>> fut(todo.size());
+        std::vector<const WPlanHost *> ready(todo.size(), nullptr);
         for (size_t i = 0; i < todo.size(); ++i) {
-            WPlanHost hp = fut[i].get();
-            plan_for(*todo[i].first, todo[i].second, &hp);
+            if (pre) ready[i] = pre->find(todo[i].first == &matA_ ? 0 : 1, todo[i].second);
+            if (!ready[i]) fut[i] = std::async(std::launch::async, host_plan, std::cref(todo[i].first->rp), todo[i].second);
+        }
+        for (size_t i = 0; i < todo.size(); ++i) {
+            if (ready[i]) {
+                plan_for(*todo[i].first, todo[i].second, ready[i]);
+            } else {
+                WPlanHost hp = fut[i].get();
+                plan_for(*todo[i].first, todo[i].second, &hp);
+            }
         }
     }
 
     const WDev &plan_for(const MatPlans &mp, int grid, const WPlanHost *prebuilt = nullptr) const {
         auto it = mp.by_grid.find(grid);
         if (it != mp.by_grid.end()) return it->second;
-        const WPlanHost hp = prebuilt ? *prebuilt : host_plan(mp, grid);
+        const WPlanHost hp = prebuilt ? *prebuilt : host_plan(mp.rp, grid);
         WDev d;
         d.nwarps = hp.nwarps;
         d.nsplit = (int)hp.split.size();
@@ -1693,13 +1784,6 @@ private:
     }
     // CTAs of a warp-stream kernel: as many as fit at once, fewer when the
     // matrix is small (at least about 512 nonzeros per warp)
-    int grid_for_rows(const std::vector<int> &rp, const void *kernel) const {
-        int per_sm = 0;
-        GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0));
-        const long long work = (rp.empty() ? 0LL : (long long)rp.back()) + 16LL * (long long)(rp.size() - 1);
-        const long long want = (work + (long long)kWWarps * 512 - 1) / ((long long)kWWarps * 512);
-        return (int)std::max(1LL, std::min<long long>(want, (long long)device_sm_count() * std::max(per_sm, 1)));
-    }
     // rs from the scaled bounds, and the weighted column sums it implies
     void rho_vector_setup() {
         if (m) launch(k_rho_scale<T>, ceil_div(m, 256), 256, stream_, (const T *)l_.as<T>(), (const T *)u_.as<T>(), m,
@@ -1916,9 +2000,12 @@ private:
 
 }  // namespace
 
-std::unique_ptr<EngineBase> make_engine(SetupData &&sd, const gbosqp_settings &s, cudaStream_t stream) {
-    if (s.precision == GBOSQP_FP64) return std::unique_ptr<EngineBase>(new Engine<double>(std::move(sd), s, stream));
-    return std::unique_ptr<EngineBase>(new Engine<float>(std::move(sd), s, stream));
+std::unique_ptr<EngineBase> make_engine(SetupData &&sd, const gbosqp_settings &s, cudaStream_t stream,
+                                        std::shared_ptr<PlanPrefetch> pre) {
+    if (pre) pre->wait();  // every host thread done before the row pointers move
+    if (s.precision == GBOSQP_FP64)
+        return std::unique_ptr<EngineBase>(new Engine<double>(std::move(sd), s, stream, pre.get()));
+    return std::unique_ptr<EngineBase>(new Engine<float>(std::move(sd), s, stream, pre.get()));
 }
 
 }  // namespace gb

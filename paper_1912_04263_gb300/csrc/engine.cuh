@@ -2,6 +2,7 @@
 // engine (engine.cu) and the C ABI (api.cu).
 #pragma once
 
+#include <functional>
 #include <memory>
 #include <vector>
 
@@ -24,9 +25,21 @@ struct SetupData {
     double qnorm_u = 0.0;  // max_i |q_bar_i| / D_i  (times 1/c = ||q||_inf)
 };
 
+// Called by device_setup with the host row pointers of A and [P A'] as soon
+// as they are known (before equilibration); the vectors are the callee's.
+using RowptrHook = std::function<void(std::vector<int> &&A_rowptr, std::vector<int> &&PAt_rowptr)>;
+
 // Build SetupData from validated inputs (see osqp_setup).  Throws GbError.
+// With a hook, the host row pointers go to the hook instead of SetupData.
 SetupData device_setup(const gbosqp_csr &P, const gbosqp_csr &A, const double *q, const double *l,
-                       const double *u, const gbosqp_settings &s, cudaStream_t stream);
+                       const double *u, const gbosqp_settings &s, cudaStream_t stream,
+                       const RowptrHook &hook = RowptrHook());
+
+// Host plans of the SpMV kernels, built on host threads from the row
+// pointers while the device equilibrates, and handed to make_engine.
+struct PlanPrefetch;
+std::shared_ptr<PlanPrefetch> start_plans(const gbosqp_settings &s, std::vector<int> &&A_rowptr,
+                                          std::vector<int> &&PAt_rowptr);
 
 class EngineBase {
 public:
@@ -64,6 +77,7 @@ public:
     long long nnzA = 0, nnzPAt = 0, nnzP = 0;
 };
 
-std::unique_ptr<EngineBase> make_engine(SetupData &&sd, const gbosqp_settings &s, cudaStream_t stream);
+std::unique_ptr<EngineBase> make_engine(SetupData &&sd, const gbosqp_settings &s, cudaStream_t stream,
+                                        std::shared_ptr<PlanPrefetch> pre = nullptr);
 
 }  // namespace gb

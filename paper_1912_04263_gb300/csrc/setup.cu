@@ -119,6 +119,80 @@ __global__ void k_check_vectors(const double *q, int n, const double *l, const d
     }
 }
 
+// ------------------------------------------------------------ long rows
+// The row-wise set-up passes give a warp to each row of at most kLongRow
+// nonzeros (counted over the one or two matrices a pass reads) and a CTA to
+// each longer row, from a list built once per matrix, so that a few very
+// long rows (the columns of a dense-ish data matrix, as rows of A') do not
+// leave the GPU with a handful of warps streaming them.  Maxima and
+// elementwise passes give the same results either way; sums are added in a
+// fixed order in both.
+constexpr int kLongRow = 2048;
+
+struct LongRows {
+    DevBuf flag;   // per row: 1 when the row takes a CTA
+    DevBuf list;   // those rows, in no particular order
+    DevBuf count;  // how many
+    int grid = 1;  // CTAs of the long-row kernels
+};
+
+__global__ void k_long_rows(const int *rp1, const int *rp2, int nrows, int *flag, int *list, int *count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nrows) return;
+    int len = rp1[i + 1] - rp1[i];
+    if (rp2) len += rp2[i + 1] - rp2[i];
+    const int f = len > kLongRow ? 1 : 0;
+    flag[i] = f;
+    if (f) list[atomicAdd(count, 1)] = i;
+}
+
+LongRows long_rows(const int *rp1, const int *rp2, int nrows, long long nnz, cudaStream_t st) {
+    LongRows L;
+    L.flag.alloc(sizeof(int) * (size_t)std::max(nrows, 1));
+    L.list.alloc(sizeof(int) * (size_t)std::max(nrows, 1));
+    L.count.alloc(sizeof(int));
+    GB_CUDA(cudaMemsetAsync(L.count.p, 0, sizeof(int), st));
+    GB_CUDA(cudaMemsetAsync(L.flag.p, 0, L.flag.bytes, st));
+    if (nrows > 0) launch(k_long_rows, blocks_for(nrows, 256), 256, st, rp1, rp2, nrows, L.flag.as<int>(),
+                          L.list.as<int>(), L.count.as<int>());
+    // at most nnz / kLongRow rows are long
+    L.grid = (int)std::max(1LL, std::min<long long>(nnz / kLongRow + 1, (long long)device_sm_count() * 8));
+    return L;
+}
+
+// Maximum of non-negative doubles on their bit patterns (integer pipe).
+__device__ __forceinline__ double nmax(double a, double b) {
+    const long long x = __double_as_longlong(a), y = __double_as_longlong(b);
+    return __longlong_as_double(x > y ? x : y);
+}
+
+// Maxima of non-negative doubles and sums over a CTA, in a fixed order;
+// every thread gets the result.
+__device__ double block_max(double v) {
+    __shared__ double sh[kWarps];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = nmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double r = sh[0];
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) r = nmax(r, sh[k]);
+    return r;
+}
+__device__ double block_sum(double v) {
+    __shared__ double sh[kWarps];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double r = sh[0];
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) r += sh[k];
+    return r;
+}
+
 // ----------------------------------------------------------------- scan
 
 __global__ void k_scan_block(const int *in, int n, int *out, int *bsum) {
@@ -365,21 +439,16 @@ __device__ __forceinline__ double limit_scaling(double v) {
 }
 
 // Norms of the equilibrated matrices from the unscaled ones and the scaling
-// so far (the matrices are scaled once, after the last pass).  Maxima of
-// non-negative values on their bit patterns (integer pipe).
-__device__ __forceinline__ double nmax(double a, double b) {
-    const long long x = __double_as_longlong(a), y = __double_as_longlong(b);
-    return __longlong_as_double(x > y ? x : y);
-}
+// so far (the matrices are scaled once, after the last pass).
 
 // Columns j < n of [[P_bar, A_bar'], [A_bar, 0]]: out[j] = D_j max(c max_k
 // |P_jk| D_k, max_i |A'_ji| E_i), one warp per j (rows of P and of A').
 __global__ void k_norm_x(const int *prp, const int *pcol, const double *pval, const int *arp, const int *acol,
                          const double *aval, int n, const double *D, const double *E, const double *scal,
-                         double *out) {
+                         double *out, const int *skip) {
     const int j = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
-    if (j >= n) return;
+    if (j >= n || skip[j]) return;
     double mp = 0.0, ma = 0.0;
     for (int k = prp[j] + lane; k < prp[j + 1]; k += 32) mp = nmax(mp, fabs(pval[k]) * D[pcol[k]]);
     for (int k = arp[j] + lane; k < arp[j + 1]; k += 32) ma = nmax(ma, fabs(aval[k]) * E[acol[k]]);
@@ -390,18 +459,41 @@ __global__ void k_norm_x(const int *prp, const int *pcol, const double *pval, co
     }
     if (lane == 0) out[j] = D[j] * nmax(scal[0] * mp, ma);
 }
+__global__ void k_norm_x_long(const int *prp, const int *pcol, const double *pval, const int *arp, const int *acol,
+                              const double *aval, const int *list, const int *count, const double *D,
+                              const double *E, const double *scal, double *out) {
+    for (int l = blockIdx.x; l < *count; l += gridDim.x) {
+        const int j = list[l];
+        double mp = 0.0, ma = 0.0;
+        for (int k = prp[j] + threadIdx.x; k < prp[j + 1]; k += blockDim.x) mp = nmax(mp, fabs(pval[k]) * D[pcol[k]]);
+        for (int k = arp[j] + threadIdx.x; k < arp[j + 1]; k += blockDim.x) ma = nmax(ma, fabs(aval[k]) * E[acol[k]]);
+        mp = block_max(mp);
+        ma = block_max(ma);
+        if (threadIdx.x == 0) out[j] = D[j] * nmax(scal[0] * mp, ma);
+    }
+}
 
 // Columns n + i (rows of A_bar): out[i] = E_i max_j |A_ij| D_j.
 __global__ void k_norm_z(const int *rp, const int *col, const double *val, int m, const double *D, const double *E,
-                         double *out) {
+                         double *out, const int *skip) {
     const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
-    if (i >= m) return;
+    if (i >= m || skip[i]) return;
     double mx = 0.0;
     for (int k = rp[i] + lane; k < rp[i + 1]; k += 32) mx = nmax(mx, fabs(val[k]) * D[col[k]]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = nmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
     if (lane == 0) out[i] = E[i] * mx;
+}
+__global__ void k_norm_z_long(const int *rp, const int *col, const double *val, const int *list, const int *count,
+                              const double *D, const double *E, double *out) {
+    for (int l = blockIdx.x; l < *count; l += gridDim.x) {
+        const int i = list[l];
+        double mx = 0.0;
+        for (int k = rp[i] + threadIdx.x; k < rp[i + 1]; k += blockDim.x) mx = nmax(mx, fabs(val[k]) * D[col[k]]);
+        mx = block_max(mx);
+        if (threadIdx.x == 0) out[i] = E[i] * mx;
+    }
 }
 
 // delta = 1/sqrt(limit(norm)); accumulated scaling *= delta.
@@ -416,12 +508,20 @@ __global__ void k_delta(const double *norm, int n, double *delta, double *acc) {
 // M <- g diag(rs) M diag(cs), one warp per row: v = (v * (g rs[r])) * cs[c]
 // (g = *gp, or 1 when gp is null).
 __global__ void k_scale_csr(const int *rp, const int *col, double *val, int nrows, const double *rs,
-                            const double *cs, const double *gp) {
+                            const double *cs, const double *gp, const int *skip) {
     const int r = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
-    if (r >= nrows) return;
+    if (r >= nrows || skip[r]) return;
     const double a = (gp ? *gp : 1.0) * rs[r];
     for (int k = rp[r] + lane; k < rp[r + 1]; k += 32) val[k] = (val[k] * a) * cs[col[k]];
+}
+__global__ void k_scale_csr_long(const int *rp, const int *col, double *val, const int *list, const int *count,
+                                 const double *rs, const double *cs, const double *gp) {
+    for (int l = blockIdx.x; l < *count; l += gridDim.x) {
+        const int r = list[l];
+        const double a = (gp ? *gp : 1.0) * rs[r];
+        for (int k = rp[r] + threadIdx.x; k < rp[r + 1]; k += blockDim.x) val[k] = (val[k] * a) * cs[col[k]];
+    }
 }
 
 // q_bar = c D q
@@ -485,10 +585,10 @@ __global__ void k_pat_rowptr(const int *prp, const int *atrp, int n, int *patrp,
 
 __global__ void k_pat_fill(const int *prp, const int *pcol, const double *pval, const int *atrp,
                            const int *atcol, const double *atval, int n, const int *patrp, int *patcol,
-                           double *patval) {
+                           double *patval, const int *skip) {
     const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
-    if (i >= n) return;
+    if (i >= n || skip[i]) return;
     int out = patrp[i];
     const int p0 = prp[i], np = prp[i + 1] - p0;
     for (int k = lane; k < np; k += 32) {
@@ -502,13 +602,32 @@ __global__ void k_pat_fill(const int *prp, const int *pcol, const double *pval, 
         patval[out + k] = atval[a0 + k];
     }
 }
+__global__ void k_pat_fill_long(const int *prp, const int *pcol, const double *pval, const int *atrp,
+                                const int *atcol, const double *atval, int n, const int *list, const int *count,
+                                const int *patrp, int *patcol, double *patval) {
+    for (int l = blockIdx.x; l < *count; l += gridDim.x) {
+        const int i = list[l];
+        int out = patrp[i];
+        const int p0 = prp[i], np = prp[i + 1] - p0;
+        for (int k = threadIdx.x; k < np; k += blockDim.x) {
+            patcol[out + k] = pcol[p0 + k];
+            patval[out + k] = pval[p0 + k];
+        }
+        out += np;
+        const int a0 = atrp[i], na = atrp[i + 1] - a0;
+        for (int k = threadIdx.x; k < na; k += blockDim.x) {
+            patcol[out + k] = atcol[a0 + k] + n;
+            patval[out + k] = atval[a0 + k];
+        }
+    }
+}
 
 // diag(P_bar) and ||A_bar column i||_2^2 (row i of A_bar'), one warp per i.
 __global__ void k_diag_colsq(const int *prp, const int *pcol, const double *pval, const int *atrp,
-                             const double *atval, int n, double *diagP, double *colsq) {
+                             const double *atval, int n, double *diagP, double *colsq, const int *skip) {
     const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
-    if (i >= n) return;
+    if (i >= n || skip[i]) return;
     double d = 0.0, s = 0.0;
     for (int k = prp[i] + lane; k < prp[i + 1]; k += 32)
         if (pcol[k] == i) d = pval[k];
@@ -523,13 +642,40 @@ __global__ void k_diag_colsq(const int *prp, const int *pcol, const double *pval
         colsq[i] = s;
     }
 }
+__global__ void k_diag_colsq_long(const int *prp, const int *pcol, const double *pval, const int *atrp,
+                                  const double *atval, const int *list, const int *count, double *diagP,
+                                  double *colsq) {
+    for (int l = blockIdx.x; l < *count; l += gridDim.x) {
+        const int i = list[l];
+        double d = 0.0, s = 0.0;
+        for (int k = prp[i] + threadIdx.x; k < prp[i + 1]; k += blockDim.x)
+            if (pcol[k] == i) d = pval[k];
+        for (int k = atrp[i] + threadIdx.x; k < atrp[i + 1]; k += blockDim.x) s += atval[k] * atval[k];
+        d = block_sum(d);
+        s = block_sum(s);
+        if (threadIdx.x == 0) {
+            diagP[i] = d;
+            colsq[i] = s;
+        }
+    }
+}
 
 __global__ void k_qnorms(const double *q, const double *D, int n, unsigned long long *out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double a = fabs(q[i]);
-    atomicMax(out, (unsigned long long)__double_as_longlong(a));
-    atomicMax(out + 1, (unsigned long long)__double_as_longlong(a / D[i]));
+    double a = 0.0, b = 0.0;
+    if (i < n) {
+        a = fabs(q[i]);
+        b = a / D[i];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a = nmax(a, __shfl_down_sync(0xffffffffu, a, o));
+        b = nmax(b, __shfl_down_sync(0xffffffffu, b, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(out, (unsigned long long)__double_as_longlong(a));
+        atomicMax(out + 1, (unsigned long long)__double_as_longlong(b));
+    }
 }
 
 // ------------------------------------------------------------ host pieces
@@ -602,7 +748,7 @@ int flag_code(int f) {
 }  // namespace
 
 SetupData device_setup(const gbosqp_csr &P, const gbosqp_csr &A, const double *q, const double *l,
-                       const double *u, const gbosqp_settings &s, cudaStream_t st) {
+                       const double *u, const gbosqp_settings &s, cudaStream_t st, const RowptrHook &hook) {
     const int n = P.nrows, m = A.nrows;
     const bool host = s.input_location == GBOSQP_HOST;
     SetupData sd;
@@ -684,6 +830,30 @@ SetupData device_setup(const gbosqp_csr &P, const gbosqp_csr &A, const double *q
     Pin = Csr();
     Csr At = transpose(Ain.rp.as<int>(), Ain.col.as<int>(), Ain.val.as<double>(), m, n, Ain.nnz, st);
     sd.nnzP = Pf.nnz;
+    // rows of [P A'] and of A that the row-wise passes give a CTA each
+    const LongRows LP = long_rows(Pf.rp.as<int>(), At.rp.as<int>(), n, Pf.nnz + At.nnz, st);
+    const LongRows LA = long_rows(Ain.rp.as<int>(), nullptr, m, Ain.nnz, st);
+    // the row pointer of [P A'] (structure only), and both row pointers on
+    // the host: with a hook the SpMV plans are built from them on host
+    // threads while the device runs the equilibration below
+    sd.nnzPAt = Pf.nnz + At.nnz;
+    if (sd.nnzPAt >= (1LL << 31) - 256 || A.nnz >= (1LL << 31) - 256)
+        fail(GBOSQP_ERR_UNSUPPORTED, "2^31 - 256 or more nonzeros in A or [P A']");
+    sd.PAt_rowptr.alloc((size_t)(n + 1) * sizeof(int));
+    sd.PAt_pend.alloc((size_t)std::max(n, 1) * sizeof(int));
+    launch(k_pat_rowptr, blocks_for(n + 1, 256), 256, st, Pf.rp.as<int>(), At.rp.as<int>(), n,
+                                                          sd.PAt_rowptr.as<int>(), sd.PAt_pend.as<int>());
+    sd.A_rowptr_host.resize(m + 1);
+    sd.PAt_rowptr_host.resize(n + 1);
+    GB_CUDA(cudaMemcpyAsync(sd.A_rowptr_host.data(), Ain.rp.p, (m + 1) * sizeof(int), cudaMemcpyDeviceToHost, st));
+    GB_CUDA(cudaMemcpyAsync(sd.PAt_rowptr_host.data(), sd.PAt_rowptr.p, (n + 1) * sizeof(int),
+                            cudaMemcpyDeviceToHost, st));
+    if (hook) {
+        GB_CUDA(cudaStreamSynchronize(st));
+        hook(std::move(sd.A_rowptr_host), std::move(sd.PAt_rowptr_host));
+        sd.A_rowptr_host.clear();
+        sd.PAt_rowptr_host.clear();
+    }
 
     // ---- 3. Ruiz equilibration (Algorithm 2)
     sd.D.alloc((size_t)std::max(n, 1) * sizeof(double));
@@ -704,9 +874,15 @@ SetupData device_setup(const gbosqp_csr &P, const gbosqp_csr &A, const double *q
         if (n) launch(k_norm_x, warp_blocks(n), kThreads, st, Pf.rp.as<int>(), Pf.col.as<int>(), Pf.val.as<double>(),
                                                             At.rp.as<int>(), At.col.as<int>(), At.val.as<double>(), n,
                                                             sd.D.as<double>(), sd.E.as<double>(), scal.as<double>(),
-                                                            nx.as<double>());
+                                                            nx.as<double>(), LP.flag.as<int>());
+        if (n) launch(k_norm_x_long, LP.grid, kThreads, st, Pf.rp.as<int>(), Pf.col.as<int>(), Pf.val.as<double>(),
+                      At.rp.as<int>(), At.col.as<int>(), At.val.as<double>(), LP.list.as<int>(), LP.count.as<int>(),
+                      sd.D.as<double>(), sd.E.as<double>(), scal.as<double>(), nx.as<double>());
         if (m) launch(k_norm_z, warp_blocks(m), kThreads, st, Ain.rp.as<int>(), Ain.col.as<int>(), Ain.val.as<double>(),
-                                                            m, sd.D.as<double>(), sd.E.as<double>(), nz.as<double>());
+                                                            m, sd.D.as<double>(), sd.E.as<double>(), nz.as<double>(),
+                                                            LA.flag.as<int>());
+        if (m) launch(k_norm_z_long, LA.grid, kThreads, st, Ain.rp.as<int>(), Ain.col.as<int>(), Ain.val.as<double>(),
+                      LA.list.as<int>(), LA.count.as<int>(), sd.D.as<double>(), sd.E.as<double>(), nz.as<double>());
         if (n) launch(k_delta, blocks_for(n, 256), 256, st, nx.as<double>(), n, dx.as<double>(), sd.D.as<double>());
         if (m) launch(k_delta, blocks_for(m, 256), 256, st, nz.as<double>(), m, dz.as<double>(), sd.E.as<double>());
         // cost scaling on P_bar = c D P D, q_bar = c D q with the new D
@@ -716,39 +892,43 @@ SetupData device_setup(const gbosqp_csr &P, const gbosqp_csr &A, const double *q
         GB_CUDA(cudaGetLastError());
     }
     // the scaled problem: P <- c D P D, A <- E A D, A' <- D A' E, q <- c D q
-    if (n) launch(k_scale_csr, warp_blocks(n), kThreads, st, Pf.rp.as<int>(), Pf.col.as<int>(), Pf.val.as<double>(), n,
-                                                           sd.D.as<double>(), sd.D.as<double>(), (const double *)scal.as<double>());
-    if (m) launch(k_scale_csr, warp_blocks(m), kThreads, st, Ain.rp.as<int>(), Ain.col.as<int>(), Ain.val.as<double>(), m,
-                                                           sd.E.as<double>(), sd.D.as<double>(), (const double *)nullptr);
-    if (n) launch(k_scale_csr, warp_blocks(n), kThreads, st, At.rp.as<int>(), At.col.as<int>(), At.val.as<double>(), n,
-                                                           sd.D.as<double>(), sd.E.as<double>(), (const double *)nullptr);
+    auto scale = [&](const Csr &M, int nrows, const LongRows &L, const double *rs, const double *cs, const double *g) {
+        if (!nrows) return;
+        launch(k_scale_csr, warp_blocks(nrows), kThreads, st, M.rp.as<int>(), M.col.as<int>(), M.val.as<double>(), nrows,
+               rs, cs, g, L.flag.as<int>());
+        launch(k_scale_csr_long, L.grid, kThreads, st, M.rp.as<int>(), M.col.as<int>(), M.val.as<double>(),
+               L.list.as<int>(), L.count.as<int>(), rs, cs, g);
+    };
+    scale(Pf, n, LP, sd.D.as<double>(), sd.D.as<double>(), (const double *)scal.as<double>());
+    scale(Ain, m, LA, sd.E.as<double>(), sd.D.as<double>(), (const double *)nullptr);
+    scale(At, n, LP, sd.D.as<double>(), sd.E.as<double>(), (const double *)nullptr);
     if (n) launch(k_scale_q_final, blocks_for(n, 256), 256, st, sd.q.as<double>(), (const double *)sd.D.as<double>(),
                                                                (const double *)scal.as<double>(), n);
     if (m) launch(k_scale_bounds, blocks_for(m, 256), 256, st, sd.l.as<double>(), sd.u.as<double>(), sd.E.as<double>(), m);
     GB_CUDA(cudaMemcpyAsync(&sd.c, scal.p, sizeof(double), cudaMemcpyDeviceToHost, st));
 
     // ---- 4. [P A'], Jacobi data, q norms
-    sd.nnzPAt = Pf.nnz + At.nnz;
-    if (sd.nnzPAt >= (1LL << 31) - 256 || A.nnz >= (1LL << 31) - 256)
-        fail(GBOSQP_ERR_UNSUPPORTED, "2^31 - 256 or more nonzeros in A or [P A']");
-    sd.PAt_rowptr.alloc((size_t)(n + 1) * sizeof(int));
-    sd.PAt_pend.alloc((size_t)std::max(n, 1) * sizeof(int));
     // kSlack zeroed elements past the last nonzero, as in the copy of A
     sd.PAt_col.alloc((sd.nnzPAt + kSlack) * sizeof(int));
     sd.PAt_val.alloc((sd.nnzPAt + kSlack) * sizeof(double));
     GB_CUDA(cudaMemsetAsync(sd.PAt_col.as<int>() + sd.nnzPAt, 0, kSlack * sizeof(int), st));
     GB_CUDA(cudaMemsetAsync(sd.PAt_val.as<double>() + sd.nnzPAt, 0, kSlack * sizeof(double), st));
-    launch(k_pat_rowptr, blocks_for(n + 1, 256), 256, st, Pf.rp.as<int>(), At.rp.as<int>(), n,
-                                                          sd.PAt_rowptr.as<int>(), sd.PAt_pend.as<int>());
     if (n) launch(k_pat_fill, warp_blocks(n), kThreads, st, Pf.rp.as<int>(), Pf.col.as<int>(), Pf.val.as<double>(),
                                                           At.rp.as<int>(), At.col.as<int>(), At.val.as<double>(), n,
                                                           sd.PAt_rowptr.as<int>(), sd.PAt_col.as<int>(),
-                                                          sd.PAt_val.as<double>());
+                                                          sd.PAt_val.as<double>(), LP.flag.as<int>());
+    if (n) launch(k_pat_fill_long, LP.grid, kThreads, st, Pf.rp.as<int>(), Pf.col.as<int>(), Pf.val.as<double>(),
+                  At.rp.as<int>(), At.col.as<int>(), At.val.as<double>(), n, LP.list.as<int>(), LP.count.as<int>(),
+                  sd.PAt_rowptr.as<int>(), sd.PAt_col.as<int>(), sd.PAt_val.as<double>());
     sd.diagP.alloc((size_t)std::max(n, 1) * sizeof(double));
     sd.colsq.alloc((size_t)std::max(n, 1) * sizeof(double));
     if (n) launch(k_diag_colsq, warp_blocks(n), kThreads, st, Pf.rp.as<int>(), Pf.col.as<int>(), Pf.val.as<double>(),
                                                             At.rp.as<int>(), At.val.as<double>(), n,
-                                                            sd.diagP.as<double>(), sd.colsq.as<double>());
+                                                            sd.diagP.as<double>(), sd.colsq.as<double>(),
+                                                            LP.flag.as<int>());
+    if (n) launch(k_diag_colsq_long, LP.grid, kThreads, st, Pf.rp.as<int>(), Pf.col.as<int>(), Pf.val.as<double>(),
+                  At.rp.as<int>(), At.val.as<double>(), LP.list.as<int>(), LP.count.as<int>(), sd.diagP.as<double>(),
+                  sd.colsq.as<double>());
     Tmp qn(2 * sizeof(unsigned long long), st);
     GB_CUDA(cudaMemsetAsync(qn.p, 0, 2 * sizeof(unsigned long long), st));
     if (n) launch(k_qnorms, blocks_for(n, 256), 256, st, sd.q.as<double>(), sd.D.as<double>(), n,
@@ -760,11 +940,6 @@ SetupData device_setup(const gbosqp_csr &P, const gbosqp_csr &A, const double *q
     sd.A_rowptr = std::move(Ain.rp);
     sd.A_col = std::move(Ain.col);
     sd.A_val = std::move(Ain.val);
-    sd.A_rowptr_host.resize(m + 1);
-    sd.PAt_rowptr_host.resize(n + 1);
-    GB_CUDA(cudaMemcpyAsync(sd.A_rowptr_host.data(), sd.A_rowptr.p, (m + 1) * sizeof(int), cudaMemcpyDeviceToHost, st));
-    GB_CUDA(cudaMemcpyAsync(sd.PAt_rowptr_host.data(), sd.PAt_rowptr.p, (n + 1) * sizeof(int),
-                            cudaMemcpyDeviceToHost, st));
     GB_CUDA(cudaStreamSynchronize(st));
     sd.qnorm_s = qnh[0];
     sd.qnorm_u = qnh[1];
