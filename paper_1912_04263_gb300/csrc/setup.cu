@@ -119,51 +119,94 @@ __global__ void k_check_vectors(const double *q, int n, const double *l, const d
     }
 }
 
-// ------------------------------------------------------------ long rows
-// The row-wise set-up passes give a warp to each row of at most kLongRow
-// nonzeros (counted over the one or two matrices a pass reads) and a CTA to
-// each longer row, from a list built once per matrix, so that a few very
-// long rows (the columns of a dense-ish data matrix, as rows of A') do not
-// leave the GPU with a handful of warps streaming them.  Maxima and
-// elementwise passes give the same results either way; sums are added in a
-// fixed order in both.
+// ------------------------------------------------------------ row tiers
+// The row-wise set-up passes share the rows out by length (counted over the
+// one or two matrices a pass reads): a thread to each row of at most
+// kThreadRow nonzeros, a warp to each row of at most kLongRow, and a CTA to
+// each longer row.  The warp and CTA rows are listed once per matrix, so
+// that neither the many short rows (one or two nonzeros in the Lasso's
+// [P A']) nor a few very long ones (its columns of D, as rows of A') leave
+// the GPU running a handful of busy lanes.  Maxima and elementwise passes
+// give the same results on every tier; sums are added in a fixed order.
+constexpr int kThreadRow = 16;
 constexpr int kLongRow = 2048;
+enum Tier { kTierThread = 0, kTierWarp = 1, kTierCta = 2 };
 
 struct LongRows {
-    DevBuf flag;   // per row: 1 when the row takes a CTA
-    DevBuf list;   // those rows, in no particular order
-    DevBuf count;  // how many
-    int grid = 1;  // CTAs of the long-row kernels
+    DevBuf flag;           // per row: its Tier
+    DevBuf list, count;    // the CTA rows, in no particular order, and how many
+    DevBuf wlist, wcount;  // the warp rows
+    int grid = 1;          // CTAs of the CTA-row kernels
 };
 
-__global__ void k_long_rows(const int *rp1, const int *rp2, int nrows, int *flag, int *list, int *count) {
+__global__ void k_long_rows(const int *rp1, const int *rp2, int nrows, int *flag, int *list, int *count, int *wlist,
+                            int *wcount) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nrows) return;
     int len = rp1[i + 1] - rp1[i];
     if (rp2) len += rp2[i + 1] - rp2[i];
-    const int f = len > kLongRow ? 1 : 0;
+    const int f = len > kLongRow ? kTierCta : len > kThreadRow ? kTierWarp : kTierThread;
     flag[i] = f;
-    if (f) list[atomicAdd(count, 1)] = i;
+    if (f == kTierCta) list[atomicAdd(count, 1)] = i;
+    if (f == kTierWarp) wlist[atomicAdd(wcount, 1)] = i;
 }
 
 LongRows long_rows(const int *rp1, const int *rp2, int nrows, long long nnz, cudaStream_t st) {
     LongRows L;
     L.flag.alloc(sizeof(int) * (size_t)std::max(nrows, 1));
     L.list.alloc(sizeof(int) * (size_t)std::max(nrows, 1));
+    L.wlist.alloc(sizeof(int) * (size_t)std::max(nrows, 1));
     L.count.alloc(sizeof(int));
+    L.wcount.alloc(sizeof(int));
     GB_CUDA(cudaMemsetAsync(L.count.p, 0, sizeof(int), st));
+    GB_CUDA(cudaMemsetAsync(L.wcount.p, 0, sizeof(int), st));
     GB_CUDA(cudaMemsetAsync(L.flag.p, 0, L.flag.bytes, st));
     if (nrows > 0) launch(k_long_rows, blocks_for(nrows, 256), 256, st, rp1, rp2, nrows, L.flag.as<int>(),
-                          L.list.as<int>(), L.count.as<int>());
+                          L.list.as<int>(), L.count.as<int>(), L.wlist.as<int>(), L.wcount.as<int>());
     // at most nnz / kLongRow rows are long
     L.grid = (int)std::max(1LL, std::min<long long>(nnz / kLongRow + 1, (long long)device_sm_count() * 8));
     return L;
+}
+
+// CTAs of a warp-row kernel: as many as fit on the GPU at once, and no more
+// than one warp per row.
+int resident_grid(const void *kernel, long long nrows) {
+    int per_sm = 0;
+    GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0));
+    const long long cap = (long long)device_sm_count() * std::max(per_sm, 1);
+    return (int)std::max(1LL, std::min<long long>((nrows + kWarps - 1) / kWarps, cap));
 }
 
 // Maximum of non-negative doubles on their bit patterns (integer pipe).
 __device__ __forceinline__ double nmax(double a, double b) {
     const long long x = __double_as_longlong(a), y = __double_as_longlong(b);
     return __longlong_as_double(x > y ? x : y);
+}
+
+// max_k |val[k]| sc[col[k]] over k in [k0, k1) taken by the thread t of a
+// group of S threads (k = k0 + t, k0 + t + S, ...), with kLd entries
+// loaded before their products are taken.  The CTA-row kernels take kLd =
+// 4 so that 8 CTAs fit on an SM and every long row of a pass runs at once.
+template <int kLd = 8>
+__device__ __forceinline__ double strided_scaled_max(const int *col, const double *val, const double *sc, int k0,
+                                                     int k1, int t, int S) {
+    double mx = 0.0;
+    for (int k = k0 + t; k < k1; k += kLd * S) {
+        double v[kLd];
+        int c[kLd];
+#pragma unroll
+        for (int u = 0; u < kLd; ++u) {
+            const int e = k + u * S;
+            v[u] = e < k1 ? val[e] : 0.0;
+            c[u] = e < k1 ? col[e] : -1;
+        }
+        double g[kLd];
+#pragma unroll
+        for (int u = 0; u < kLd; ++u) g[u] = c[u] >= 0 ? sc[c[u]] : 0.0;
+#pragma unroll
+        for (int u = 0; u < kLd; ++u) mx = nmax(mx, fabs(v[u]) * g[u]);
+    }
+    return mx;
 }
 
 // Maxima of non-negative doubles and sums over a CTA, in a fixed order;
@@ -258,31 +301,39 @@ __global__ void k_iota(int *v, long long n) {
     if (i < n) v[i] = (int)i;
 }
 
-__global__ void k_radix_hist(const int *keys, long long nnz, int shift, int ntiles, int *H) {
-    __shared__ int hist[kRsWarps][256];
+// Digits of up to kRsMaxBits bits: the key bits are split into as few
+// passes as that allows, of about equal width (17-bit column indices: two
+// passes of 9 and 8 bits instead of three of 8).
+constexpr int kRsMaxBits = 9;
+constexpr int kRsMaxDigits = 1 << kRsMaxBits;
+
+__global__ void k_radix_hist(const int *keys, long long nnz, int shift, int bits, int ntiles, int *H) {
+    __shared__ int hist[kRsWarps][kRsMaxDigits];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tile = blockIdx.x * kRsWarps + w;
-    for (int d = lane; d < 256; d += 32) hist[w][d] = 0;
+    const int nd = 1 << bits, mask = nd - 1;
+    for (int d = lane; d < nd; d += 32) hist[w][d] = 0;
     __syncwarp();
     if (tile >= ntiles) return;
     const long long base = (long long)tile * kRsTile;
     for (int it = 0; it < kRsPerLane; ++it) {
         const long long k = base + it * 32 + lane;
-        if (k < nnz) atomicAdd(&hist[w][(keys[k] >> shift) & 255], 1);
+        if (k < nnz) atomicAdd(&hist[w][(keys[k] >> shift) & mask], 1);
     }
     __syncwarp();
-    for (int d = lane; d < 256; d += 32) H[(size_t)d * ntiles + tile] = hist[w][d];
+    for (int d = lane; d < nd; d += 32) H[(size_t)d * ntiles + tile] = hist[w][d];
 }
 
 // Stable scatter: each warp walks its tile in order; equal digits within a
 // 32-key step are ranked by lane, and a per-warp running count per digit
 // carries the order across steps.
-__global__ void k_radix_scatter(const int *kin, const int *vin, long long nnz, int shift, int ntiles,
+__global__ void k_radix_scatter(const int *kin, const int *vin, long long nnz, int shift, int bits, int ntiles,
                                 const int *offs, int *kout, int *vout) {
-    __shared__ int cnt[kRsWarps][256];
+    __shared__ int cnt[kRsWarps][kRsMaxDigits];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tile = blockIdx.x * kRsWarps + w;
-    for (int d = lane; d < 256; d += 32) cnt[w][d] = 0;
+    const int nd = 1 << bits, mask = nd - 1;
+    for (int d = lane; d < nd; d += 32) cnt[w][d] = 0;
     __syncwarp();
     if (tile >= ntiles) return;
     const long long base = (long long)tile * kRsTile;
@@ -293,7 +344,7 @@ __global__ void k_radix_scatter(const int *kin, const int *vin, long long nnz, i
         if (valid) {
             key = kin[k];
             val = vin[k];
-            d = (key >> shift) & 255;
+            d = (key >> shift) & mask;
         }
         const unsigned act = __ballot_sync(0xffffffffu, valid);
         unsigned peers = 0;
@@ -320,21 +371,26 @@ void stable_sort_by_key(const int *keys, long long nnz, int max_key, int *perm, 
         vb(nnz * sizeof(int), st);
     GB_CUDA(cudaMemcpyAsync(ka.p, keys, nnz * sizeof(int), cudaMemcpyDeviceToDevice, st));
     launch(k_iota, blocks_for(nnz, 256), 256, st, va.as<int>(), nnz);
+    int key_bits = 1;
+    while (key_bits < 31 && (max_key >> key_bits) > 0) ++key_bits;
+    const int passes = (key_bits + kRsMaxBits - 1) / kRsMaxBits;
+    const int width = (key_bits + passes - 1) / passes;
     const int ntiles = ceil_div(nnz, kRsTile);
-    const long long hsz = 256LL * ntiles;
+    const long long hsz = (long long)(1 << width) * ntiles;
     Tmp H(hsz * sizeof(int), st), offs((hsz + 1) * sizeof(int), st);
     int *kin = ka.as<int>(), *kout = kb.as<int>(), *vin = va.as<int>(), *vout = vb.as<int>();
-    int shift = 0;
-    do {
+    for (int pass = 0, shift = 0; pass < passes; ++pass, shift += width) {
+        const int bits = std::min(width, key_bits - shift);
+        const long long hn = (long long)(1 << bits) * ntiles;
         const int grid = ceil_div(ntiles, kRsWarps);
-        launch(k_radix_hist, grid, kRsWarps * 32, st, kin, nnz, shift, ntiles, H.as<int>());
-        exclusive_scan(H.as<int>(), (int)hsz, offs.as<int>(), st);
-        launch(k_radix_scatter, grid, kRsWarps * 32, st, kin, vin, nnz, shift, ntiles, offs.as<int>(), kout, vout);
+        launch(k_radix_hist, grid, kRsWarps * 32, st, kin, nnz, shift, bits, ntiles, H.as<int>());
+        exclusive_scan(H.as<int>(), (int)hn, offs.as<int>(), st);
+        launch(k_radix_scatter, grid, kRsWarps * 32, st, kin, vin, nnz, shift, bits, ntiles, offs.as<int>(), kout,
+               vout);
         GB_CUDA(cudaGetLastError());
         std::swap(kin, kout);
         std::swap(vin, vout);
-        shift += 8;
-    } while (shift < 31 && (max_key >> shift) > 0);
+    }
     GB_CUDA(cudaMemcpyAsync(perm, vin, nnz * sizeof(int), cudaMemcpyDeviceToDevice, st));
     if (sorted) GB_CUDA(cudaMemcpyAsync(sorted, kin, nnz * sizeof(int), cudaMemcpyDeviceToDevice, st));
 }
@@ -445,28 +501,39 @@ __device__ __forceinline__ double limit_scaling(double v) {
 // |P_jk| D_k, max_i |A'_ji| E_i), one warp per j (rows of P and of A').
 __global__ void k_norm_x(const int *prp, const int *pcol, const double *pval, const int *arp, const int *acol,
                          const double *aval, int n, const double *D, const double *E, const double *scal,
-                         double *out, const int *skip) {
-    const int j = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (j >= n || skip[j]) return;
+                         double *out, const int *tier) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;  // thread rows
+    if (j >= n || tier[j] != kTierThread) return;
     double mp = 0.0, ma = 0.0;
-    for (int k = prp[j] + lane; k < prp[j + 1]; k += 32) mp = nmax(mp, fabs(pval[k]) * D[pcol[k]]);
-    for (int k = arp[j] + lane; k < arp[j + 1]; k += 32) ma = nmax(ma, fabs(aval[k]) * E[acol[k]]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        mp = nmax(mp, __shfl_down_sync(0xffffffffu, mp, o));
-        ma = nmax(ma, __shfl_down_sync(0xffffffffu, ma, o));
-    }
-    if (lane == 0) out[j] = D[j] * nmax(scal[0] * mp, ma);
+    for (int k = prp[j]; k < prp[j + 1]; ++k) mp = nmax(mp, fabs(pval[k]) * D[pcol[k]]);
+    for (int k = arp[j]; k < arp[j + 1]; ++k) ma = nmax(ma, fabs(aval[k]) * E[acol[k]]);
+    out[j] = D[j] * nmax(scal[0] * mp, ma);
 }
-__global__ void k_norm_x_long(const int *prp, const int *pcol, const double *pval, const int *arp, const int *acol,
+__global__ void k_norm_x_warp(const int *prp, const int *pcol, const double *pval, const int *arp, const int *acol,
+                              const double *aval, const int *wlist, const int *wcount, const double *D,
+                              const double *E, const double *scal, double *out) {
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * kWarps;
+    for (int l = blockIdx.x * kWarps + (threadIdx.x >> 5); l < *wcount; l += nw) {
+        const int j = wlist[l];
+        double mp = strided_scaled_max(pcol, pval, D, prp[j], prp[j + 1], lane, 32);
+        double ma = strided_scaled_max(acol, aval, E, arp[j], arp[j + 1], lane, 32);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mp = nmax(mp, __shfl_down_sync(0xffffffffu, mp, o));
+            ma = nmax(ma, __shfl_down_sync(0xffffffffu, ma, o));
+        }
+        if (lane == 0) out[j] = D[j] * nmax(scal[0] * mp, ma);
+    }
+}
+__global__ void __launch_bounds__(kThreads, 8) k_norm_x_long(const int *prp, const int *pcol, const double *pval, const int *arp, const int *acol,
                               const double *aval, const int *list, const int *count, const double *D,
                               const double *E, const double *scal, double *out) {
     for (int l = blockIdx.x; l < *count; l += gridDim.x) {
         const int j = list[l];
         double mp = 0.0, ma = 0.0;
-        for (int k = prp[j] + threadIdx.x; k < prp[j + 1]; k += blockDim.x) mp = nmax(mp, fabs(pval[k]) * D[pcol[k]]);
-        for (int k = arp[j] + threadIdx.x; k < arp[j + 1]; k += blockDim.x) ma = nmax(ma, fabs(aval[k]) * E[acol[k]]);
+        mp = strided_scaled_max<4>(pcol, pval, D, prp[j], prp[j + 1], threadIdx.x, blockDim.x);
+        ma = strided_scaled_max<4>(acol, aval, E, arp[j], arp[j + 1], threadIdx.x, blockDim.x);
         mp = block_max(mp);
         ma = block_max(ma);
         if (threadIdx.x == 0) out[j] = D[j] * nmax(scal[0] * mp, ma);
@@ -475,22 +542,37 @@ __global__ void k_norm_x_long(const int *prp, const int *pcol, const double *pva
 
 // Columns n + i (rows of A_bar): out[i] = E_i max_j |A_ij| D_j.
 __global__ void k_norm_z(const int *rp, const int *col, const double *val, int m, const double *D, const double *E,
-                         double *out, const int *skip) {
-    const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (i >= m || skip[i]) return;
+                         double *out, const int *tier) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;  // thread rows
+    if (i >= m || tier[i] != kTierThread) return;
     double mx = 0.0;
-    for (int k = rp[i] + lane; k < rp[i + 1]; k += 32) mx = nmax(mx, fabs(val[k]) * D[col[k]]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = nmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
-    if (lane == 0) out[i] = E[i] * mx;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) mx = nmax(mx, fabs(val[k]) * D[col[k]]);
+    out[i] = E[i] * mx;
 }
-__global__ void k_norm_z_long(const int *rp, const int *col, const double *val, const int *list, const int *count,
+__global__ void k_norm_z_warp(const int *rp, const int *col, const double *val, const int *wlist, const int *wcount,
+                              const double *D, const double *E, double *out) {
+    // a half-warp per row: two rows per warp in flight
+    const int lane = threadIdx.x & 31, hl = lane & 15;
+    const int nh = gridDim.x * kWarps * 2;
+    const int cnt = *wcount;
+    for (int l = (blockIdx.x * kWarps + (threadIdx.x >> 5)) * 2 + (lane >> 4); l - (lane >> 4) < cnt; l += nh) {
+        double mx = 0.0;
+        int i = -1;
+        if (l < cnt) {
+            i = wlist[l];
+            mx = strided_scaled_max(col, val, D, rp[i], rp[i + 1], hl, 16);
+        }
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) mx = nmax(mx, __shfl_down_sync(0xffffffffu, mx, o, 16));
+        if (hl == 0 && i >= 0) out[i] = E[i] * mx;
+    }
+}
+__global__ void __launch_bounds__(kThreads, 8) k_norm_z_long(const int *rp, const int *col, const double *val, const int *list, const int *count,
                               const double *D, const double *E, double *out) {
     for (int l = blockIdx.x; l < *count; l += gridDim.x) {
         const int i = list[l];
         double mx = 0.0;
-        for (int k = rp[i] + threadIdx.x; k < rp[i + 1]; k += blockDim.x) mx = nmax(mx, fabs(val[k]) * D[col[k]]);
+        mx = strided_scaled_max<4>(col, val, D, rp[i], rp[i + 1], threadIdx.x, blockDim.x);
         mx = block_max(mx);
         if (threadIdx.x == 0) out[i] = E[i] * mx;
     }
@@ -511,7 +593,7 @@ __global__ void k_scale_csr(const int *rp, const int *col, double *val, int nrow
                             const double *cs, const double *gp, const int *skip) {
     const int r = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
-    if (r >= nrows || skip[r]) return;
+    if (r >= nrows || skip[r] == kTierCta) return;
     const double a = (gp ? *gp : 1.0) * rs[r];
     for (int k = rp[r] + lane; k < rp[r + 1]; k += 32) val[k] = (val[k] * a) * cs[col[k]];
 }
@@ -538,16 +620,26 @@ __global__ void k_cost_scale(const int *prp, const int *pcol, const double *pval
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const double c = scal[0];
     double sum = 0.0, qmax = 0.0;
+    // rows of at most kThreadRow entries: a thread each
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const int a = prp[r], b = prp[r + 1];
+        if (b - a <= kThreadRow) {
+            double mx = 0.0;
+            for (int k = a; k < b; ++k) mx = nmax(mx, fabs(pval[k]) * D[pcol[k]]);
+            sum += c * D[r] * mx;
+        }
+        qmax = nmax(qmax, fabs(c * D[r] * q[r]));
+    }
+    // longer rows: a warp each
     const int nwarps_grid = gridDim.x * kWarps;
     for (int r = blockIdx.x * kWarps + warp; r < n; r += nwarps_grid) {
-        double mx = 0.0;
-        for (int k = prp[r] + lane; k < prp[r + 1]; k += 32) mx = nmax(mx, fabs(pval[k]) * D[pcol[k]]);
+        const int a = prp[r], b = prp[r + 1];
+        if (b - a <= kThreadRow) continue;
+        double mx = strided_scaled_max(pcol, pval, D, a, b, lane, 32);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = nmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
         if (lane == 0) sum += c * D[r] * mx;
     }
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        qmax = nmax(qmax, fabs(c * D[i] * q[i]));
     Red<1, 1> red;
     red.s[0] = sum;
     red.m[0] = qmax;
@@ -588,7 +680,7 @@ __global__ void k_pat_fill(const int *prp, const int *pcol, const double *pval, 
                            double *patval, const int *skip) {
     const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
-    if (i >= n || skip[i]) return;
+    if (i >= n || skip[i] == kTierCta) return;
     int out = patrp[i];
     const int p0 = prp[i], np = prp[i + 1] - p0;
     for (int k = lane; k < np; k += 32) {
@@ -627,7 +719,7 @@ __global__ void k_diag_colsq(const int *prp, const int *pcol, const double *pval
                              const double *atval, int n, double *diagP, double *colsq, const int *skip) {
     const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
-    if (i >= n || skip[i]) return;
+    if (i >= n || skip[i] == kTierCta) return;
     double d = 0.0, s = 0.0;
     for (int k = prp[i] + lane; k < prp[i + 1]; k += 32)
         if (pcol[k] == i) d = pval[k];
@@ -867,18 +959,24 @@ SetupData device_setup(const gbosqp_csr &P, const gbosqp_csr &A, const double *q
     launch(k_fill, blocks_for(n, 256), 256, st, sd.D.as<double>(), n, 1.0);
     launch(k_fill, blocks_for(m, 256), 256, st, sd.E.as<double>(), m, 1.0);
     launch(k_fill, 1, 32, st, scal.as<double>(), 1, 1.0);
+    const int gxw = resident_grid((const void *)k_norm_x_warp, n), gzw = resident_grid((const void *)k_norm_z_warp, m);
     for (int pass = 0; pass < s.scaling_iters; ++pass) {
         // column inf-norms of [[P_bar, A_bar'], [A_bar, 0]] from the unscaled
         // matrices and the scaling so far: columns j < n are rows of P and
         // A'; columns n + i are rows of A
-        if (n) launch(k_norm_x, warp_blocks(n), kThreads, st, Pf.rp.as<int>(), Pf.col.as<int>(), Pf.val.as<double>(),
+        if (n) launch(k_norm_x_warp, gxw, kThreads, st, Pf.rp.as<int>(), Pf.col.as<int>(), Pf.val.as<double>(),
+                      At.rp.as<int>(), At.col.as<int>(), At.val.as<double>(), LP.wlist.as<int>(), LP.wcount.as<int>(),
+                      sd.D.as<double>(), sd.E.as<double>(), scal.as<double>(), nx.as<double>());
+        if (n) launch(k_norm_x, blocks_for(n, kThreads), kThreads, st, Pf.rp.as<int>(), Pf.col.as<int>(), Pf.val.as<double>(),
                                                             At.rp.as<int>(), At.col.as<int>(), At.val.as<double>(), n,
                                                             sd.D.as<double>(), sd.E.as<double>(), scal.as<double>(),
                                                             nx.as<double>(), LP.flag.as<int>());
         if (n) launch(k_norm_x_long, LP.grid, kThreads, st, Pf.rp.as<int>(), Pf.col.as<int>(), Pf.val.as<double>(),
                       At.rp.as<int>(), At.col.as<int>(), At.val.as<double>(), LP.list.as<int>(), LP.count.as<int>(),
                       sd.D.as<double>(), sd.E.as<double>(), scal.as<double>(), nx.as<double>());
-        if (m) launch(k_norm_z, warp_blocks(m), kThreads, st, Ain.rp.as<int>(), Ain.col.as<int>(), Ain.val.as<double>(),
+        if (m) launch(k_norm_z_warp, gzw, kThreads, st, Ain.rp.as<int>(), Ain.col.as<int>(), Ain.val.as<double>(),
+                      LA.wlist.as<int>(), LA.wcount.as<int>(), sd.D.as<double>(), sd.E.as<double>(), nz.as<double>());
+        if (m) launch(k_norm_z, blocks_for(m, kThreads), kThreads, st, Ain.rp.as<int>(), Ain.col.as<int>(), Ain.val.as<double>(),
                                                             m, sd.D.as<double>(), sd.E.as<double>(), nz.as<double>(),
                                                             LA.flag.as<int>());
         if (m) launch(k_norm_z_long, LA.grid, kThreads, st, Ain.rp.as<int>(), Ain.col.as<int>(), Ain.val.as<double>(),
