@@ -231,6 +231,30 @@ __device__ __forceinline__ void add_records(Red<NS, NM> &acc, const double *tab,
     }
 }
 
+// Arrival at a grid-wide ticket, with release and acquire semantics at GPU
+// scope: the writes this thread made before (and those other threads of its
+// CTA made before a CTA barrier that precedes the call) are visible to every
+// thread that arrives later, and the writes published by earlier arrivals
+// are visible to this thread and, after a CTA barrier, to its whole CTA.
+// Returns the ticket's value before the arrival.  (A full fence before a
+// relaxed atomic, and another after it, order the same accesses at more
+// cost.)
+#ifndef GB_ACQREL
+#define GB_ACQREL 1
+#endif
+__device__ __forceinline__ unsigned int ticket_arrive(unsigned int *t) {
+#if GB_ACQREL
+    unsigned int old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(t) : "memory");
+    return old;
+#else
+    __threadfence();
+    const unsigned int old = atomicAdd(t, 1u);
+    __threadfence();
+    return old;
+#endif
+}
+
 // Per-CTA partials -> the last CTA to arrive sums them in CTA order and
 // calls fin(total) with every thread of that CTA (thread 0 holds nothing
 // special; the total is broadcast through shared memory).
@@ -246,13 +270,11 @@ __device__ __forceinline__ void grid_finish(Red<NS, NM> &red, double *partials, 
         for (int i = 0; i < NS; ++i) partials[(size_t)blockIdx.x * NR + i] = red.s[i];
 #pragma unroll
         for (int i = 0; i < NM; ++i) partials[(size_t)blockIdx.x * NR + NS + i] = red.m[i];
-        __threadfence();
-        unsigned int t = atomicAdd(ticket, 1u);
+        const unsigned int t = ticket_arrive(ticket);
         am_last = (t == gridDim.x - 1);
     }
     __syncthreads();
     if (!am_last) return;
-    __threadfence();
     Red<NS, NM> acc;
     acc.zero();
     add_records<NS, NM, NS, NM>(acc, partials, NR, (int)gridDim.x);

@@ -136,12 +136,10 @@ __device__ __forceinline__ void publish_part(const CsrW<T> &M, int l, int slot, 
     if (lane == 0) {
         M.split_part[2 * (size_t)slot] = (double)t1;
         M.split_part[2 * (size_t)slot + 1] = (double)t2;
-        __threadfence();
         const SplitRow S = M.split[l];
-        const int t = atomicAdd(M.split_count + l, 1);
+        const int t = (int)ticket_arrive(reinterpret_cast<unsigned int *>(M.split_count + l));
         last = t == S.nparts - 1;
         if (last) {
-            __threadfence();
             double s1 = 0.0, s2 = 0.0;
             for (int k = 0; k < S.nparts; ++k) {
                 s1 += __ldcg(M.split_part + 2 * (size_t)(S.slot0 + k));
@@ -157,7 +155,7 @@ __device__ __forceinline__ void publish_part(const CsrW<T> &M, int l, int slot, 
             for (int i = 0; i < NM; ++i) red.m[i] = amax(red.m[i], tmp.m[i]);
 #pragma unroll
             for (int i = 0; i < NS; ++i) M.split_red[(size_t)l * kMaxSplitSums + i] = tmp.s[i];
-            __threadfence();
+            // seen by the grid total through the CTA barrier before thread 0 arrives at its ticket
         }
     }
     (void)last;
@@ -447,13 +445,11 @@ __device__ __forceinline__ void grid_finish_w(Red<NS, NM> &red, const CsrW<T> &M
         for (int i = 0; i < NS; ++i) partials[(size_t)blockIdx.x * NR + i] = red.s[i];
 #pragma unroll
         for (int i = 0; i < NM; ++i) partials[(size_t)blockIdx.x * NR + NS + i] = red.m[i];
-        __threadfence();
-        const unsigned int t = atomicAdd(ticket, 1u);
+        const unsigned int t = ticket_arrive(ticket);
         am_last = (t == gridDim.x - 1);
     }
     __syncthreads();
     if (!am_last) return;
-    __threadfence();
     Red<NS, NM> acc;
     acc.zero();
     add_records<NS, NM, NS, NM>(acc, partials, NR, (int)gridDim.x);
