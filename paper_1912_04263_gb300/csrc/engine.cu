@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : 2) k_p
     }
     EpiDir<T> epi{v.pt + n, v.rs, T(st->rho)};
     Red<0, 0> red;
-    warp_rows<kU, T, false>(A, GatherDir<T>{v.ypc, beta}, epi, red);
+    warp_rows<kU, T, false, true>(A, GatherDir<T>{v.ypc, beta}, epi, red);
 }
 
 // Kp = P p + sigma p + A' t;  p'Kp.  A row cut between warps contributes
@@ -445,7 +445,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : 2)
     }
     EpiDir<T> epi{v.pt + n, v.rs, T(st->rho)};
     Red<0, 0> none;
-    warp_rows<kU, T, false>(A, GatherSr<T>{S, a, b}, epi, none);
+    warp_rows<kU, T, false, true>(A, GatherSr<T>{S, a, b}, epi, none);
     auto fin = [&](const Red<1, 1> &t) {
         if (threadIdx.x != 0) return;
         st->ry_prev = st->ry;
@@ -550,7 +550,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : 2) k_a
     }
     EpiAdmm<T> epi{v, alpha, rho, T(1.0 / st->rho)};
     Red<0, 0> red;
-    warp_rows<kU, T, false>(A, GatherVec<T, T>{v.xt}, epi, red);
+    warp_rows<kU, T, false, true>(A, GatherVec<T, T>{v.xt}, epi, red);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->k += 1;
         st->cg_since_update += st->cg_it;
@@ -580,7 +580,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_check_a(Cs
     EpiCheckA<T> epi{v};
     Red<0, 6> red;
     red.zero();
-    warp_rows<kU, double, false>(A, GatherVec<T, T>{v.xy}, epi, red);
+    warp_rows<kU, double, false, true>(A, GatherVec<T, T>{v.xy}, epi, red);
     auto fin = [&](const Red<0, 6> &t) {
         if (threadIdx.x == 0)
             for (int i = 0; i < 6; ++i) st->c1[i] = t.m[i];
@@ -620,7 +620,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_inf_a(CsrW
     EpiInfA<T> epi{v};
     Red<1, 3> red;
     red.zero();
-    warp_rows<kU, T, false>(A, GatherVec<T, T>{v.dxy}, epi, red);
+    warp_rows<kU, T, false, true>(A, GatherVec<T, T>{v.dxy}, epi, red);
     auto fin = [&](const Red<1, 3> &t) {
         if (threadIdx.x != 0) return;
         st->inf_a[0] = t.m[0];

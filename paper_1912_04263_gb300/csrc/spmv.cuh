@@ -196,7 +196,7 @@ __device__ __forceinline__ void split_part(const CsrW<T> &M, int l, int slot, in
 // item (the matrix arrays carry kSlack zeroed elements past the last
 // nonzero), and those lanes' products are discarded.  The next batch of U
 // steps is loaded while the current one is summed.
-template <int U, class Acc, bool SPLIT, class T, class Gather, class Epi, class RedT>
+template <int U, class Acc, bool SPLIT, bool EDGE, class T, class Gather, class Epi, class RedT>
 __device__ __forceinline__ void stream_item(const CsrW<T> &M, const WItem &it, const WSplit &ws,
                                             const Gather &gather, Epi &epi, RedT &red) {
     using namespace wdetail;
@@ -284,12 +284,24 @@ __device__ __forceinline__ void stream_item(const CsrW<T> &M, const WItem &it, c
 #endif
     // add the products of the U steps from s0 to their rows
     auto sum_batch = [&](int s0, T(&pr)[U]) {
+        // EDGE (see warp_rows): only the first and the last batch hold steps
+        // that reach outside the item or past its last step, so the others
+        // skip those masks
+        const bool edge = !EDGE || s0 == 0 || s0 + U >= nsteps;
+        if (EDGE && edge) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int s = s0 + u;
+                const int e = base + (s << 5) + lane;
+                if (s < nsteps && (s == 0 || s == nsteps - 1) && (e < kbeg || e >= kend)) pr[u] = T(0);
+            }
+        }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int s = s0 + u;
-            if (s >= nsteps) break;
+            if (edge && s >= nsteps) break;
             const int e = base + (s << 5) + lane;
-            if ((s == 0 || s == nsteps - 1) && (e < kbeg || e >= kend)) pr[u] = T(0);
+            if (!EDGE && (s == 0 || s == nsteps - 1) && (e < kbeg || e >= kend)) pr[u] = T(0);
             if (s != cross) {
                 if (!SPLIT || e < pcur) a1.add(pr[u]); else a2.add(pr[u]);
             } else {
@@ -403,8 +415,11 @@ __device__ __forceinline__ void group_item(const CsrW<T> &M, int r0, int r1, con
     }
 }
 
-// The whole range of this warp.
-template <int U, class Acc, bool SPLIT, class T, class Gather, class Epi, class RedT>
+// The whole range of this warp.  EDGE: the stream path tests a batch once
+// for reaching past its item instead of testing every step (measured: the
+// kernels over A, with rows of about 150 nonzeros, gain; the [P A'] kernels,
+// whose long parts run in few large batches, lose to the extra code).
+template <int U, class Acc, bool SPLIT, bool EDGE = false, class T, class Gather, class Epi, class RedT>
 __device__ __forceinline__ void warp_rows(const CsrW<T> &M, const Gather &gather, Epi &epi, RedT &red) {
     const int w = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
     const int i0 = M.wpart[w], i1 = M.wpart[w + 1];
@@ -413,7 +428,7 @@ __device__ __forceinline__ void warp_rows(const CsrW<T> &M, const Gather &gather
     for (int i = i0; i < i1; ++i) {
         const WItem it = M.items[i];
         if (it.k0 >= 0) {
-            stream_item<U, Acc, SPLIT>(M, it, ws, gather, epi, red);
+            stream_item<U, Acc, SPLIT, EDGE>(M, it, ws, gather, epi, red);
         } else {
             switch (-it.k0) {
 #ifndef GB_GROUP_R
