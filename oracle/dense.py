@@ -83,8 +83,11 @@ class DenseSchurFactor:
         self.At = self.A.T.tocsr()
         self.K = sp.bmat([[P + sigma * sp.identity(n), A.T],
                           [A, sp.diags(-1.0 / self.r) if m else None]], format="csr")
-        self.cho = la.cho_factor(schur_matrix(P, A, sigma, self.r), lower=True, overwrite_a=True,
+        L, lower = la.cho_factor(schur_matrix(P, A, sigma, self.r), lower=True, overwrite_a=True,
                                  check_finite=False)
+        # kept in Fortran order: LAPACK's solve would otherwise get a transposed
+        # copy of the whole factor on every call
+        self.cho = (np.asfortranarray(L), lower)
         self.max_rel_residual = 0.0
 
     def _solve_once(self, rhs: np.ndarray) -> np.ndarray:
