@@ -63,6 +63,34 @@ struct Tmp {
     template <class T> T *as() const { return static_cast<T *>(p); }
 };
 
+// A second stream that runs beside st: fork() makes it wait for st's work
+// so far and returns it; join() makes st wait for what was queued on it.
+struct SideStream {
+    cudaStream_t st, side = nullptr;
+    cudaEvent_t forked = nullptr, joined = nullptr;
+    explicit SideStream(cudaStream_t s) : st(s) {
+        GB_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+        GB_CUDA(cudaEventCreateWithFlags(&forked, cudaEventDisableTiming));
+        GB_CUDA(cudaEventCreateWithFlags(&joined, cudaEventDisableTiming));
+    }
+    ~SideStream() {
+        if (joined) cudaEventDestroy(joined);
+        if (forked) cudaEventDestroy(forked);
+        if (side) cudaStreamDestroy(side);
+    }
+    SideStream(const SideStream &) = delete;
+    SideStream &operator=(const SideStream &) = delete;
+    cudaStream_t fork() {
+        GB_CUDA(cudaEventRecord(forked, st));
+        GB_CUDA(cudaStreamWaitEvent(side, forked, 0));
+        return side;
+    }
+    void join() {
+        GB_CUDA(cudaEventRecord(joined, side));
+        GB_CUDA(cudaStreamWaitEvent(st, joined, 0));
+    }
+};
+
 inline int blocks_for(long long n, int threads) { return (int)std::max(1LL, (n + threads - 1) / threads); }
 inline int warp_blocks(long long rows) { return (int)std::max(1LL, (rows + kWarps - 1) / kWarps); }
 
@@ -960,18 +988,22 @@ SetupData device_setup(const gbosqp_csr &P, const gbosqp_csr &A, const double *q
     launch(k_fill, blocks_for(m, 256), 256, st, sd.E.as<double>(), m, 1.0);
     launch(k_fill, 1, 32, st, scal.as<double>(), 1, 1.0);
     const int gxw = resident_grid((const void *)k_norm_x_warp, n), gzw = resident_grid((const void *)k_norm_z_warp, m);
+    // the norms of the columns j < n and of the columns n + i run side by
+    // side: those of x on a second stream, joined by events
+    SideStream side(st);
     for (int pass = 0; pass < s.scaling_iters; ++pass) {
         // column inf-norms of [[P_bar, A_bar'], [A_bar, 0]] from the unscaled
         // matrices and the scaling so far: columns j < n are rows of P and
         // A'; columns n + i are rows of A
-        if (n) launch(k_norm_x_warp, gxw, kThreads, st, Pf.rp.as<int>(), Pf.col.as<int>(), Pf.val.as<double>(),
+        const cudaStream_t sx = side.fork();
+        if (n) launch(k_norm_x_warp, gxw, kThreads, sx, Pf.rp.as<int>(), Pf.col.as<int>(), Pf.val.as<double>(),
                       At.rp.as<int>(), At.col.as<int>(), At.val.as<double>(), LP.wlist.as<int>(), LP.wcount.as<int>(),
                       sd.D.as<double>(), sd.E.as<double>(), scal.as<double>(), nx.as<double>());
-        if (n) launch(k_norm_x, blocks_for(n, kThreads), kThreads, st, Pf.rp.as<int>(), Pf.col.as<int>(), Pf.val.as<double>(),
+        if (n) launch(k_norm_x, blocks_for(n, kThreads), kThreads, sx, Pf.rp.as<int>(), Pf.col.as<int>(), Pf.val.as<double>(),
                                                             At.rp.as<int>(), At.col.as<int>(), At.val.as<double>(), n,
                                                             sd.D.as<double>(), sd.E.as<double>(), scal.as<double>(),
                                                             nx.as<double>(), LP.flag.as<int>());
-        if (n) launch(k_norm_x_long, LP.grid, kThreads, st, Pf.rp.as<int>(), Pf.col.as<int>(), Pf.val.as<double>(),
+        if (n) launch(k_norm_x_long, LP.grid, kThreads, sx, Pf.rp.as<int>(), Pf.col.as<int>(), Pf.val.as<double>(),
                       At.rp.as<int>(), At.col.as<int>(), At.val.as<double>(), LP.list.as<int>(), LP.count.as<int>(),
                       sd.D.as<double>(), sd.E.as<double>(), scal.as<double>(), nx.as<double>());
         if (m) launch(k_norm_z_warp, gzw, kThreads, st, Ain.rp.as<int>(), Ain.col.as<int>(), Ain.val.as<double>(),
@@ -981,6 +1013,7 @@ SetupData device_setup(const gbosqp_csr &P, const gbosqp_csr &A, const double *q
                                                             LA.flag.as<int>());
         if (m) launch(k_norm_z_long, LA.grid, kThreads, st, Ain.rp.as<int>(), Ain.col.as<int>(), Ain.val.as<double>(),
                       LA.list.as<int>(), LA.count.as<int>(), sd.D.as<double>(), sd.E.as<double>(), nz.as<double>());
+        side.join();  // both sides read D and E; the deltas below rewrite them
         if (n) launch(k_delta, blocks_for(n, 256), 256, st, nx.as<double>(), n, dx.as<double>(), sd.D.as<double>());
         if (m) launch(k_delta, blocks_for(m, 256), 256, st, nz.as<double>(), m, dz.as<double>(), sd.E.as<double>());
         // cost scaling on P_bar = c D P D, q_bar = c D q with the new D
