@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : 2) k_p
     EpiInit<T> epi{v, T(st->sigma)};
     Red<1, 1> red;
     red.zero();
-    warp_rows<kU, T, false>(PAt, GatherVec<T, T>{v.xt}, epi, red);
+    warp_rows<kU, T, false, false, true>(PAt, GatherVec<T, T>{v.xt}, epi, red);
     auto fin = [&](const Red<1, 1> &t) {
         if (threadIdx.x != 0) return;
         st->ry = t.s[0];

@@ -128,7 +128,7 @@ __device__ __forceinline__ int win_get(int win, int nwin, int idx) {
 // the row to arrive, sum the parts in slot order and run the row's
 // epilogue; its sums go to split_red[l] so that the grid total adds them in
 // a fixed order.
-template <class Acc, class T, class Epi, class RedT>
+template <class Acc, bool HOIST = false, class T, class Epi, class RedT>
 __device__ __forceinline__ void publish_part(const CsrW<T> &M, int l, int slot, int row, Acc t1, Acc t2, Epi &epi,
                                              RedT &red) {
     const int lane = threadIdx.x & 31;
@@ -141,9 +141,29 @@ __device__ __forceinline__ void publish_part(const CsrW<T> &M, int l, int slot, 
         last = t == S.nparts - 1;
         if (last) {
             double s1 = 0.0, s2 = 0.0;
-            for (int k = 0; k < S.nparts; ++k) {
-                s1 += __ldcg(M.split_part + 2 * (size_t)(S.slot0 + k));
-                s2 += __ldcg(M.split_part + 2 * (size_t)(S.slot0 + k) + 1);
+            if constexpr (HOIST) {
+                // the parts' loads issued kLd at a time, then added in slot order
+                constexpr int kLd = 4;
+                for (int k0 = 0; k0 < S.nparts; k0 += kLd) {
+                    double a[kLd], b[kLd];
+#pragma unroll
+                    for (int u = 0; u < kLd; ++u) {
+                        const bool in = k0 + u < S.nparts;
+                        a[u] = in ? __ldcg(M.split_part + 2 * (size_t)(S.slot0 + k0 + u)) : 0.0;
+                        b[u] = in ? __ldcg(M.split_part + 2 * (size_t)(S.slot0 + k0 + u) + 1) : 0.0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kLd; ++u)
+                        if (k0 + u < S.nparts) {
+                            s1 += a[u];
+                            s2 += b[u];
+                        }
+                }
+            } else {
+                for (int k = 0; k < S.nparts; ++k) {
+                    s1 += __ldcg(M.split_part + 2 * (size_t)(S.slot0 + k));
+                    s2 += __ldcg(M.split_part + 2 * (size_t)(S.slot0 + k) + 1);
+                }
             }
             M.split_count[l] = 0;
             RedT tmp;
@@ -173,7 +193,7 @@ template <class E>
 struct SplitParts<E, std::void_t<decltype(E::kSplitParts)>> : std::integral_constant<bool, E::kSplitParts> {};
 
 // One warp's part of split row l, in slot `slot`.
-template <class Acc, class T, class Epi, class RedT>
+template <class Acc, bool HOIST = false, class T, class Epi, class RedT>
 __device__ __forceinline__ void split_part(const CsrW<T> &M, int l, int slot, int row, Acc t1, Acc t2, Epi &epi,
                                            RedT &red) {
     if constexpr (SplitParts<Epi>::value) {
@@ -183,7 +203,7 @@ __device__ __forceinline__ void split_part(const CsrW<T> &M, int l, int slot, in
             epi.part(row, slot == M.split[l].slot0, t1, t2, red);
         }
     } else {
-        publish_part<Acc>(M, l, slot, row, t1, t2, epi, red);
+        publish_part<Acc, HOIST>(M, l, slot, row, t1, t2, epi, red);
     }
 }
 
@@ -196,7 +216,7 @@ __device__ __forceinline__ void split_part(const CsrW<T> &M, int l, int slot, in
 // item (the matrix arrays carry kSlack zeroed elements past the last
 // nonzero), and those lanes' products are discarded.  The next batch of U
 // steps is loaded while the current one is summed.
-template <int U, class Acc, bool SPLIT, bool EDGE, class T, class Gather, class Epi, class RedT>
+template <int U, class Acc, bool SPLIT, bool EDGE, bool HOIST, class T, class Gather, class Epi, class RedT>
 __device__ __forceinline__ void stream_item(const CsrW<T> &M, const WItem &it, const WSplit &ws,
                                             const Gather &gather, Epi &epi, RedT &red) {
     using namespace wdetail;
@@ -236,8 +256,8 @@ __device__ __forceinline__ void stream_item(const CsrW<T> &M, const WItem &it, c
     auto finish_row = [&](int r, Acc t1, Acc t2) {
         if (r == head_row || r == tail_row) {
             const WSplit w2 = M.wsplit[wid];  // reloaded: keeps the split ids out of the loop's registers
-            if (r == head_row) split_part<Acc>(M, w2.head, w2.head_slot, r, t1, t2, epi, red);
-            else split_part<Acc>(M, w2.tail, w2.tail_slot, r, t1, t2, epi, red);
+            if (r == head_row) split_part<Acc, HOIST>(M, w2.head, w2.head_slot, r, t1, t2, epi, red);
+            else split_part<Acc, HOIST>(M, w2.tail, w2.tail_slot, r, t1, t2, epi, red);
         } else {
             if (lane == npend) {
                 prow = r;
@@ -415,11 +435,14 @@ __device__ __forceinline__ void group_item(const CsrW<T> &M, int r0, int r1, con
     }
 }
 
-// The whole range of this warp.  EDGE: the stream path tests a batch once
+// The whole range of this warp.  HOIST: the last warp of a row cut between
+// warps loads the parts together (measured: the PCG initialisation gains,
+// kernels with heavier register use lose).  EDGE: the stream path tests a batch once
 // for reaching past its item instead of testing every step (measured: the
 // kernels over A, with rows of about 150 nonzeros, gain; the [P A'] kernels,
 // whose long parts run in few large batches, lose to the extra code).
-template <int U, class Acc, bool SPLIT, bool EDGE = false, class T, class Gather, class Epi, class RedT>
+template <int U, class Acc, bool SPLIT, bool EDGE = false, bool HOIST = false, class T, class Gather, class Epi,
+          class RedT>
 __device__ __forceinline__ void warp_rows(const CsrW<T> &M, const Gather &gather, Epi &epi, RedT &red) {
     const int w = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
     const int i0 = M.wpart[w], i1 = M.wpart[w + 1];
@@ -428,7 +451,7 @@ __device__ __forceinline__ void warp_rows(const CsrW<T> &M, const Gather &gather
     for (int i = i0; i < i1; ++i) {
         const WItem it = M.items[i];
         if (it.k0 >= 0) {
-            stream_item<U, Acc, SPLIT, EDGE>(M, it, ws, gather, epi, red);
+            stream_item<U, Acc, SPLIT, EDGE, HOIST>(M, it, ws, gather, epi, red);
         } else {
             switch (-it.k0) {
 #ifndef GB_GROUP_R
