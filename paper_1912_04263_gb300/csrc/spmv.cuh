@@ -4,7 +4,8 @@
 // in contiguous ranges of about equal cost (nonzeros plus a fixed cost per
 // row).  A cut between two warps may fall inside a long row; the parts of
 // such a split row are summed by the last of its warps to finish, in warp
-// order, so every result is bitwise reproducible.
+// order (or, for epilogues that take a split row by parts, stored in fixed
+// slots for a later kernel), so every result is bitwise reproducible.
 //
 // Inside its range a warp walks items of two kinds:
 // * stream items: consecutive rows of more than 32 nonzeros (and the parts
