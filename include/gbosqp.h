@@ -379,9 +379,14 @@ int gbosqp_resume(gbosqp_handle *h);
 #define GBOSQP_K_PCG_UPDATE 2     /* x, r, M^{-1} r updates, r'y, ||r|| (vectors, n)    */
 #define GBOSQP_K_PCG_INIT 3       /* r = K x - b from [P A'] and t0 (SpMV [P A'])       */
 #define GBOSQP_K_ADMM_UPDATE 4    /* z~ = A x~, projection, dual update (SpMV A)        */
-#define GBOSQP_K_CHECK_A 5        /* ||Ax - z|| etc., FP64 accumulation (SpMV A)        */
+#define GBOSQP_K_CHECK_A 5        /* ||Ax - z|| etc., FP64 accumulation (SpMV A); the
+                                     solve runs it when infeasibility detection is off */
 #define GBOSQP_K_CHECK_B 6        /* ||Px + q + A'y|| etc., FP64 (SpMV [P A'])          */
-#define GBOSQP_K_INF_A 7          /* A dx against the bounds, dy clipping (SpMV A)       */
+#define GBOSQP_K_INF_A 7          /* the rows of A of the check and of the detection in
+                                     one pass gathering x and dx: ||Ax - z|| etc. as
+                                     GBOSQP_K_CHECK_A, A dx against the bounds, dy
+                                     clipping (SpMV A); the solve runs it in place of
+                                     GBOSQP_K_CHECK_A when detection is on          */
 #define GBOSQP_K_INF_B 8          /* ||P dx||, ||A'dy||, q'dx (SpMV [P A'])              */
 #define GBOSQP_K_PCG_SR_DIRECTION 9 /* single-reduction PCG: p, s = K p, x, r, M^{-1} r
                                        updates, r'y, ||r||, t = rho A M^{-1} r (SpMV A) */

@@ -114,6 +114,10 @@ struct Vecs {
     int n, m;
 };
 
+// doubles of the per-CTA record of a grid reduction (sums then maxima) that
+// the partials buffer holds for every CTA of the largest grid
+constexpr int kPartialRecord = 16;
+
 // resident CTAs per SM requested for the row-block kernels of the PCG loop
 // (bounds registers so that enough loads are in flight per SM)
 #ifndef GB_MIN_BLOCKS
@@ -158,6 +162,15 @@ template <class T, class Acc>
 struct GatherVec {
     const T *v;
     __device__ __forceinline__ Acc operator()(int c) const { return Acc(__ldg(v + c)); }
+};
+
+// x and dx at column c together (the SpMV core sums both products)
+template <class T>
+struct GatherDual {
+    static constexpr bool kDual = true;
+    const T *v, *w;
+    __device__ __forceinline__ T operator()(int c) const { return __ldg(v + c); }
+    __device__ __forceinline__ T second(int c) const { return __ldg(w + c); }
 };
 
 template <class T>
@@ -561,18 +574,21 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? kMinBlocks : 2) k_a
 template <class T>
 struct EpiCheckA {
     Vecs<T> v;
-    __device__ __forceinline__ void row(int j, double s1, double, Red<0, 6> &red) {
+    // the six maxima of row j into red.m[M0 .. M0 + 6)
+    template <int M0, class R>
+    __device__ __forceinline__ void check(int j, double s1, R &red) const {
         const double z = to_acc<double>(v.z[j]);
         const double rp = fabs(s1 - z);
         const double ax = fabs(s1), az = fabs(z);
         const double ei = v.Einv[j];
-        red.m[0] = amax(red.m[0], rp);
-        red.m[1] = amax(red.m[1], ax);
-        red.m[2] = amax(red.m[2], az);
-        red.m[3] = amax(red.m[3], rp * ei);
-        red.m[4] = amax(red.m[4], ax * ei);
-        red.m[5] = amax(red.m[5], az * ei);
+        red.m[M0 + 0] = amax(red.m[M0 + 0], rp);
+        red.m[M0 + 1] = amax(red.m[M0 + 1], ax);
+        red.m[M0 + 2] = amax(red.m[M0 + 2], az);
+        red.m[M0 + 3] = amax(red.m[M0 + 3], rp * ei);
+        red.m[M0 + 4] = amax(red.m[M0 + 4], ax * ei);
+        red.m[M0 + 5] = amax(red.m[M0 + 5], az * ei);
     }
+    __device__ __forceinline__ void row(int j, double s1, double, Red<0, 6> &red) { check<0>(j, s1, red); }
 };
 
 template <class T>
@@ -598,37 +614,61 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_check_a(Cs
 template <class T>
 struct EpiInfA {
     Vecs<T> v;
-    __device__ __forceinline__ void row(int j, T s1, T, Red<1, 3> &red) {
+    // row j's three maxima into red.m[M0 .. M0 + 3), the support into red.s[0]
+    template <int M0, class R>
+    __device__ __forceinline__ void detect(int j, T s1, R &red) const {
         const int n = v.n;
         const double ad = to_acc<double>(s1) * v.Einv[j];
         const T l = v.l[j], u = v.u[j];
         const bool lfin = l > -T(INFINITY), ufin = u < T(INFINITY);
-        if (ufin) red.m[0] = amax(red.m[0], ad);    // keeps max(0, ...)
-        if (lfin) red.m[1] = amax(red.m[1], -ad);
+        if (ufin) red.m[M0 + 0] = amax(red.m[M0 + 0], ad);    // keeps max(0, ...)
+        if (lfin) red.m[M0 + 1] = amax(red.m[M0 + 1], -ad);
         T dy = v.dxy[n + j];
         if (!ufin && dy > T(0)) dy = T(0);
         if (!lfin && dy < T(0)) dy = T(0);
         v.dxy[n + j] = dy;
-        red.m[2] = amax(red.m[2], absd(dy) * v.E[j]);
+        red.m[M0 + 2] = amax(red.m[M0 + 2], absd(dy) * v.E[j]);
         if (dy > T(0)) red.s[0] += to_acc<double>(u) * to_acc<double>(dy);
         else if (dy < T(0)) red.s[0] += to_acc<double>(l) * to_acc<double>(dy);
     }
 };
 
+#ifndef GB_CHECK_INF_BLOCKS
+#define GB_CHECK_INF_BLOCKS 2
+#endif
+
+// With detection on, the rows of A of the termination check and of the
+// detection in one pass over A that gathers x and dx together: (A x)_j
+// summed as k_check_a sums it, (A dx)_j in the working precision as a
+// detection pass of its own would sum it (so both results are bitwise
+// those of the two separate passes), and A's values and columns read once.
+// dx holds the variables' differences only (columns < n); the rows write
+// the clipped dy at n + j.
 template <class T>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2) k_inf_a(CsrW<T> A, Vecs<T> v, Status *st, double *partials) {
-    EpiInfA<T> epi{v};
-    Red<1, 3> red;
+struct EpiCheckInfA {
+    Vecs<T> v;
+    __device__ __forceinline__ void row(int j, double ax, double adx, Red<1, 9> &red) {
+        EpiCheckA<T>{v}.template check<0>(j, ax, red);
+        EpiInfA<T>{v}.template detect<6>(j, T(adx), red);
+    }
+};
+
+template <class T>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? GB_CHECK_INF_BLOCKS : 2) k_check_inf_a(CsrW<T> A, Vecs<T> v, Status *st, double *partials) {
+    static_assert(1 + 9 <= kPartialRecord, "record wider than the partials buffer holds");
+    EpiCheckInfA<T> epi{v};
+    Red<1, 9> red;
     red.zero();
-    warp_rows<kU, T, false, true>(A, GatherVec<T, T>{v.dxy}, epi, red);
-    auto fin = [&](const Red<1, 3> &t) {
+    warp_rows<kU, double, false, true>(A, GatherDual<T>{v.xy, v.dxy}, epi, red);
+    auto fin = [&](const Red<1, 9> &t) {
         if (threadIdx.x != 0) return;
-        st->inf_a[0] = t.m[0];
-        st->inf_a[1] = t.m[1];
-        st->inf_a[2] = t.m[2];
+        for (int i = 0; i < 6; ++i) st->c1[i] = t.m[i];
+        st->inf_a[0] = t.m[6];
+        st->inf_a[1] = t.m[7];
+        st->inf_a[2] = t.m[8];
         st->inf_a[3] = t.s[0];
     };
-    grid_finish_w<1, 3>(red, A, partials, &st->tickets[kTkInfA], fin);
+    grid_finish_w<1, 9>(red, A, partials, &st->tickets[kTkC1], fin);
 }
 
 // Part B (rows of [P A']): ||D^-1 P_bar dx_bar|| and ||D^-1 A_bar' dy_bar||
@@ -1028,7 +1068,7 @@ Grids solve_grids(const std::vector<int> &rpA, const std::vector<int> &rpP, bool
     g.pt = grid_for_rows(rpA, (const void *)k_pcg_p_t<T>);
     g.admm = grid_for_rows(rpA, (const void *)k_admm_update<T>);
     g.ca = grid_for_rows(rpA, (const void *)k_check_a<T>);
-    g.ia = grid_for_rows(rpA, (const void *)k_inf_a<T>);
+    g.ia = grid_for_rows(rpA, (const void *)k_check_inf_a<T>);
     g.spA = grid_for_rows(rpA, (const void *)k_spmv<T, T>);
     g.kp = grid_for_rows(rpP, (const void *)k_pcg_kp<T>);
     g.init = grid_for_rows(rpP, (const void *)k_pcg_init<T>);
@@ -1172,7 +1212,7 @@ public:
         gridN_ = std::max(1, std::min(grid_for_n(std::max(n, m), kThreads * 4), cap));
         const int maxgrid = std::max({gPt_, gAdmm_, gCa_, gKp_, gInit_, gCb_, gIa_, gIb_, gridN_, gridVec_, gSr1_, gSr2_});
         build_plans(G.over_A(sr_), G.over_PAt(sr_), pre);
-        partials_.alloc(sizeof(double) * (size_t)maxgrid * 8);
+        partials_.alloc(sizeof(double) * (size_t)maxgrid * kPartialRecord);
         // status block
         Status h;
         std::memset(&h, 0, sizeof(h));
@@ -1575,7 +1615,7 @@ public:
                 case GBOSQP_K_ADMM_UPDATE: launch_smem(k_admm_update<T>, gAdmm_, kThreads, kSmemT, stream_, csrA(gAdmm_), v, st); break;
                 case GBOSQP_K_CHECK_A: launch_smem(k_check_a<T>, gCa_, kThreads, kSmemD, stream_, csrA(gCa_), v, st, partials_.as<double>()); break;
                 case GBOSQP_K_CHECK_B: launch_smem(k_check_b<T>, gCb_, kThreads, kSmemDS, stream_, csrPAt(gCb_), v, st, partials_.as<double>(), policy(), (cudaGraphConditionalHandle)0, 0); break;
-                case GBOSQP_K_INF_A: launch_smem(k_inf_a<T>, gIa_, kThreads, kSmemT, stream_, csrA(gIa_), v, st, partials_.as<double>()); break;
+                case GBOSQP_K_INF_A: launch_smem(k_check_inf_a<T>, gIa_, kThreads, kSmemD, stream_, csrA(gIa_), v, st, partials_.as<double>()); break;
                 case GBOSQP_K_INF_B: launch_smem(k_inf_b<T>, gIb_, kThreads, kSmemT, stream_, csrPAt(gIb_), v, st, partials_.as<double>()); break;
                 case GBOSQP_K_PCG_SR_DIRECTION:
                     if (!sr_) fail(GBOSQP_ERR_INVALID_ARG, "the handle does not use the single-reduction PCG");
@@ -1872,10 +1912,11 @@ private:
         GB_CUDA(cudaGetLastError());
     }
     void launch_check(const Vecs<T> &v, Status *st, cudaGraphConditionalHandle h, int use_h) {
-        launch_smem(k_check_a<T>, gCa_, kThreads, kSmemD, stream_, csrA(gCa_), v, st, partials_.as<double>());
-        if (inf_on_) {
-            launch_smem(k_inf_a<T>, gIa_, kThreads, kSmemT, stream_, csrA(gIa_), v, st, partials_.as<double>());
+        if (inf_on_) {  // the check's and the detection's rows of A in one pass
+            launch_smem(k_check_inf_a<T>, gIa_, kThreads, kSmemD, stream_, csrA(gIa_), v, st, partials_.as<double>());
             launch_smem(k_inf_b<T>, gIb_, kThreads, kSmemT, stream_, csrPAt(gIb_), v, st, partials_.as<double>());
+        } else {
+            launch_smem(k_check_a<T>, gCa_, kThreads, kSmemD, stream_, csrA(gCa_), v, st, partials_.as<double>());
         }
         launch_smem(k_check_b<T>, gCb_, kThreads, kSmemDS, stream_, csrPAt(gCb_), v, st, partials_.as<double>(), policy(), h, use_h);
         GB_CUDA(cudaGetLastError());
@@ -1936,10 +1977,12 @@ private:
             }
             prev = add_kernel_smem(body, &nw, k_admm_update<T>, gAdmm_, kSmemT, csrA(gAdmm_), v, st);
         }
-        cudaGraphNode_t ca = add_kernel_smem(body, &prev, k_check_a<T>, gCa_, kSmemD, csrA(gCa_), v, st, part);
-        if (inf_on_) {
-            ca = add_kernel_smem(body, &ca, k_inf_a<T>, gIa_, kSmemT, csrA(gIa_), v, st, part);
+        cudaGraphNode_t ca;
+        if (inf_on_) {  // the check's and the detection's rows of A in one pass
+            ca = add_kernel_smem(body, &prev, k_check_inf_a<T>, gIa_, kSmemD, csrA(gIa_), v, st, part);
             ca = add_kernel_smem(body, &ca, k_inf_b<T>, gIb_, kSmemT, csrPAt(gIb_), v, st, part);
+        } else {
+            ca = add_kernel_smem(body, &prev, k_check_a<T>, gCa_, kSmemD, csrA(gCa_), v, st, part);
         }
         cudaGraphNode_t cb = add_kernel_smem(body, &ca, k_check_b<T>, gCb_, kSmemDS, csrPAt(gCb_), v, st, part, policy(), hA, 1);
         add_kernel(body, &cb, k_rho_apply<T>, gridN_, v, (const Status *)st);

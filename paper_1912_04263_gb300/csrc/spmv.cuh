@@ -23,7 +23,8 @@
 //
 // The epilogue functor's row(r, s1, s2, red) consumes a row's sums (s1 over
 // the first segment [rowptr[r], pend[r]), s2 over the rest, when a split
-// point pend is given; otherwise s2 = 0) and adds to the warp's reduction.
+// point pend is given; with a gather of two vectors, s2 is the row's sum
+// with the second; otherwise s2 = 0) and adds to the warp's reduction.
 #pragma once
 
 #include <type_traits>
@@ -193,6 +194,17 @@ struct SplitParts : std::false_type {};
 template <class E>
 struct SplitParts<E, std::void_t<decltype(E::kSplitParts)>> : std::integral_constant<bool, E::kSplitParts> {};
 
+// A gather with a second vector (Gather::kDual, Gather::second(c)): the core
+// also sums the products with the second vector, in the working precision T
+// as a kernel over that vector alone would, and hands each row's second sum
+// to the epilogue as s2 (exactly, as Acc).  Only for kernels without a row
+// split point (SPLIT = false), whose s2 is otherwise zero; a row cut between
+// warps carries it through the same slot.
+template <class G, class = void>
+struct DualGather : std::false_type {};
+template <class G>
+struct DualGather<G, std::void_t<decltype(G::kDual)>> : std::integral_constant<bool, G::kDual> {};
+
 // One warp's part of split row l, in slot `slot`.
 template <class Acc, bool HOIST = false, class T, class Epi, class RedT>
 __device__ __forceinline__ void split_part(const CsrW<T> &M, int l, int slot, int row, Acc t1, Acc t2, Epi &epi,
@@ -245,7 +257,10 @@ __device__ __forceinline__ void stream_item(const CsrW<T> &M, const WItem &it, c
     const int tail_row = ws.tail >= 0 ? M.split[ws.tail].row : -1;
     const int wid = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
 
+    constexpr bool DUAL = DualGather<Gather>::value;
+    static_assert(!(DUAL && SPLIT), "a second vector's sums take the place of the split point's");
     LaneSum<Acc, T> a1, a2, b1, b2;
+    LaneSum<T, T> q1, q2;  // DUAL: the second vector's sums of the current and the next row
     // finished rows waiting for their epilogue, one per lane
     int prow = -1, npend = 0;
     Acc p1 = Acc(0), p2 = Acc(0);
@@ -304,7 +319,7 @@ __device__ __forceinline__ void stream_item(const CsrW<T> &M, const WItem &it, c
     };
 #endif
     // add the products of the U steps from s0 to their rows
-    auto sum_batch = [&](int s0, T(&pr)[U]) {
+    auto sum_batch = [&](int s0, T(&pr)[U], T(&pq)[U]) {
         // EDGE (see warp_rows): only the first and the last batch hold steps
         // that reach outside the item or past its last step, so the others
         // skip those masks
@@ -314,7 +329,10 @@ __device__ __forceinline__ void stream_item(const CsrW<T> &M, const WItem &it, c
             for (int u = 0; u < U; ++u) {
                 const int s = s0 + u;
                 const int e = base + (s << 5) + lane;
-                if (s < nsteps && (s == 0 || s == nsteps - 1) && (e < kbeg || e >= kend)) pr[u] = T(0);
+                if (s < nsteps && (s == 0 || s == nsteps - 1) && (e < kbeg || e >= kend)) {
+                    pr[u] = T(0);
+                    if (DUAL) pq[u] = T(0);
+                }
             }
         }
 #pragma unroll
@@ -322,24 +340,34 @@ __device__ __forceinline__ void stream_item(const CsrW<T> &M, const WItem &it, c
             const int s = s0 + u;
             if (edge && s >= nsteps) break;
             const int e = base + (s << 5) + lane;
-            if (!EDGE && (s == 0 || s == nsteps - 1) && (e < kbeg || e >= kend)) pr[u] = T(0);
+            if (!EDGE && (s == 0 || s == nsteps - 1) && (e < kbeg || e >= kend)) {
+                pr[u] = T(0);
+                if (DUAL) pq[u] = T(0);
+            }
             if (s != cross) {
                 if (!SPLIT || e < pcur) a1.add(pr[u]); else a2.add(pr[u]);
+                if (DUAL) q1.add(pq[u]);
             } else {
                 // row `row` ends at rend inside this step; the next row is in the item
                 const int pnext = SPLIT ? win_get(pwin, npwin, row + 1 - wbase) : 0;
                 if (e < rend) {
                     if (!SPLIT || e < pcur) a1.add(pr[u]); else a2.add(pr[u]);
+                    if (DUAL) q1.add(pq[u]);
                 } else {
                     if (!SPLIT || e < pnext) b1.add(pr[u]); else b2.add(pr[u]);
+                    if (DUAL) q2.add(pq[u]);
                 }
                 const Acc t1 = warp_allsum(a1.value());
-                const Acc t2 = SPLIT ? warp_allsum(a2.value()) : Acc(0);
+                const Acc t2 = SPLIT ? warp_allsum(a2.value()) : DUAL ? to_acc<Acc>(warp_allsum(q1.value())) : Acc(0);
                 finish_row(row, t1, t2);
                 a1 = b1;
                 a2 = b2;
                 b1 = LaneSum<Acc, T>();
                 b2 = LaneSum<Acc, T>();
+                if (DUAL) {
+                    q1 = q2;
+                    q2 = LaneSum<T, T>();
+                }
                 ++row;
                 if (row - wbase == 32) {
                     wbase += 32;
@@ -354,10 +382,13 @@ __device__ __forceinline__ void stream_item(const CsrW<T> &M, const WItem &it, c
         }
     };
     auto process = [&](int s0, const T(&v)[U], const int(&c)[U]) {
-        T pr[U];
+        T pr[U], pq[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) pr[u] = v[u] * gather(c[u]);
-        sum_batch(s0, pr);
+        for (int u = 0; u < U; ++u) {
+            pr[u] = v[u] * gather(c[u]);
+            if constexpr (DUAL) pq[u] = v[u] * gather.second(c[u]);
+        }
+        sum_batch(s0, pr, pq);
     };
     load(0, va, ca);
     for (int s0 = 0; s0 < nsteps; s0 += 2 * U) {
@@ -369,7 +400,7 @@ __device__ __forceinline__ void stream_item(const CsrW<T> &M, const WItem &it, c
     }
     // the last row ends with the item
     const Acc t1 = warp_allsum(a1.value());
-    const Acc t2 = SPLIT ? warp_allsum(a2.value()) : Acc(0);
+    const Acc t2 = SPLIT ? warp_allsum(a2.value()) : DUAL ? to_acc<Acc>(warp_allsum(q1.value())) : Acc(0);
     finish_row(row, t1, t2);
     flush();
 }
@@ -379,6 +410,8 @@ __device__ __forceinline__ void stream_item(const CsrW<T> &M, const WItem &it, c
 template <int G, int R, class Acc, bool SPLIT, class T, class Gather, class Epi, class RedT>
 __device__ __forceinline__ void group_item(const CsrW<T> &M, int r0, int r1, const Gather &gather, Epi &epi,
                                            RedT &red) {
+    constexpr bool DUAL = wdetail::DualGather<Gather>::value;
+    static_assert(!(DUAL && SPLIT), "a second vector's sums take the place of the split point's");
     constexpr int kRows = 32 / G;
     const int lane = threadIdx.x & 31;
     const int gi = lane / G, gl = lane % G;
@@ -414,22 +447,27 @@ __device__ __forceinline__ void group_item(const CsrW<T> &M, int r0, int r1, con
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             LaneSum<Acc, T> s1, s2;
+            LaneSum<T, T> sq;  // DUAL: the second vector's sum
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
                 if (c[k][u] >= 0) {
                     const T pr = v[k][u] * gather(c[k][u]);
                     const int e = a[k] + gl + u * G;
                     if (!SPLIT || e < sp[k]) s1.add(pr); else s2.add(pr);
+                    if constexpr (DUAL) sq.add(v[k][u] * gather.second(c[k][u]));
                 }
             }
             Acc t1 = s1.value(), t2 = s2.value();
+            T tq = sq.value();
             if (G > 1) {
 #pragma unroll
                 for (int o = G / 2; o > 0; o >>= 1) {
                     t1 += __shfl_down_sync(wdetail::kFull, t1, o, G);
                     if (SPLIT) t2 += __shfl_down_sync(wdetail::kFull, t2, o, G);
+                    if (DUAL) tq += __shfl_down_sync(wdetail::kFull, tq, o, G);
                 }
             }
+            if (DUAL) t2 = to_acc<Acc>(tq);
             const int r = base + k * kRows + gi;
             if (gl == 0 && r < r1) epi.row(r, t1, t2, red);
         }

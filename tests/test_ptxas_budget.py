@@ -62,7 +62,7 @@ def report():
 def test_every_solve_kernel_was_reported(report):
     names = " ".join(report)
     for k in ["k_pcg_init", "k_pcg_p_t", "k_pcg_kp", "k_pcg_update", "k_admm_update", "k_check_a", "k_check_b",
-              "k_inf_a", "k_inf_b", "k_rho_apply", "k_output"]:
+              "k_check_inf_a", "k_inf_b", "k_rho_apply", "k_output"]:
         assert k in names, k
 
 
@@ -75,12 +75,15 @@ def test_no_unexpected_spills(report):
 def test_register_counts_fit_the_launch_bounds(report):
     """256 threads per CTA and a 65536-register file: the FP32 SpMV
     kernels of the PCG loop are bounded to 4 resident CTAs per SM (64
-    registers a thread), the FP32 checks and detection kernels to 3 (80), the
-    FP64 instantiations to 2 (128); nothing may need more than 128."""
+    registers a thread), the FP32 checks and detection kernels to 3 (80) but
+    the check fused with the detection over A to 2 (128), the FP64
+    instantiations to 2 (128); nothing may need more than 128."""
     for name, r in report.items():
         regs = r.get("regs", 0)
         assert regs <= 128, (name, r)
         if any(k in name for k in ("k_pcg_p_tIfE", "k_pcg_kpIfE", "k_pcg_initIfE", "k_admm_updateIfE")):
             assert regs <= 64, (name, r)
-        if any(k in name for k in ("k_check_aIfE", "k_check_bIfE", "k_inf_aIfE", "k_inf_bIfE")):
+        if "k_check_inf_a" in name:
+            continue
+        if any(k in name for k in ("k_check_aIfE", "k_check_bIfE", "k_inf_bIfE")):
             assert regs <= 80, (name, r)
