@@ -1294,11 +1294,13 @@ public:
         if (exec_) {
             // kernels executed by the graph: reset, output, per iteration
             // pcg_init and admm_update, per PCG step three kernels, per
-            // check three kernels (five with infeasibility detection)
+            // check three kernels (four with infeasibility detection: the
+            // pass over A takes the detection's rows too, and the
+            // detection's pass over [P A'] is added)
             const long long checks = s_.check_every > 0 ? h.k / s_.check_every : 0;
             // single reduction: a pair of kernels per step plus the first pair of each PCG solve
             const long long pcg = sr_ ? 2LL * (h.cg_total + h.k) : 3LL * h.cg_total;
-            solve_launches += 2 + 2LL * h.k + pcg + (inf_on_ ? 5LL : 3LL) * checks;
+            solve_launches += 2 + 2LL * h.k + pcg + (inf_on_ ? 4LL : 3LL) * checks;
         }
         return h.status;
     }

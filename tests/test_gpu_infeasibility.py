@@ -85,10 +85,11 @@ def test_detection_off_runs_to_max_iter_and_launches_fewer_kernels():
         assert s.solve() == gb.PRIMAL_INFEASIBLE
         on = s.info()
     assert off["iters"] == 200 and on["iters"] < 200
-    # each check runs two detection kernels more
+    # each check runs one kernel more: the pass over A takes the detection's
+    # rows of A with the check's, and the detection's pass over [P A'] is added
     checks = on["iters"] // 5
     base = 2 + 2 * on["iters"] + 3 * on["pcg_iters"]
-    assert on["solve_launches"] == base + 5 * checks
+    assert on["solve_launches"] == base + 4 * checks
     checks = off["iters"] // 5
     assert off["solve_launches"] == 2 + 2 * off["iters"] + 3 * off["pcg_iters"] + 3 * checks
 
@@ -100,10 +101,14 @@ def test_graph_and_host_loop_agree_on_infeasible(prec):
         for mode in (gb.LOOP_GRAPH, gb.LOOP_HOST):
             with gb.Solver(qp, precision=prec, loop_mode=mode) as s:
                 st = s.solve()
-                out.append((st, s.info()["iters"], s.solution()))
+                info = s.info()
+                out.append((st, info["iters"], s.solution(), info["solve_launches"]))
         assert out[0][0] == out[1][0] and out[0][1] == out[1][1]
         for a, b in zip(out[0][2], out[1][2]):
             np.testing.assert_array_equal(a, b)
+        # the graph's kernel count (from the iteration counters) is the number
+        # of kernels the host-driven loop launched one by one
+        assert out[0][3] == out[1][3]
 
 
 @pytest.mark.parametrize("name", ["random_300x3000", "lasso_50x2000", "portfolio_3000x30", "equality_200x100"])
